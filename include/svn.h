@@ -1,0 +1,183 @@
+/*
+ * svn.h -- C ABI of the GB300 stress-velocity Newton (svN) solver for the
+ * implicitly discretised viscous-plastic sea-ice momentum equation
+ * (Shih, Mehlmann, Losch, Stadler: "Robust and efficient primal-dual Newton-
+ * Krylov solvers for viscous-plastic sea-ice models", arXiv:2204.10822).
+ *
+ * One implicit Euler step of the momentum equation (Section 3, Eqs. "Av=F",
+ * "A", "F") is the minimiser of the convex energy Phi (Eq. "energy").  svn_step
+ * computes it with the paper's stress-velocity Newton method (Section 4.2):
+ * the dual variable pi (Eq. "pi") lives at the quadrature points and is
+ * eliminated from each linearisation (Eqs. "tautilde", "linearSVNewton"),
+ * the fourth-order tensor is symmetrised and scaled (Eq. "modification"),
+ * each linear system is solved by FGMRES with a multigrid preconditioner
+ * (Section 5.4), and steps are damped by backtracking on Phi (Section 5.1).
+ *
+ * Discretisation.  Omega = (0, L)^2 split into N x N square cells, dx = L/N;
+ * Q1 velocity at the (N+1)^2 nodes with v = 0 on the boundary; ice thickness
+ * H (here "h") and concentration A constant per cell; 2 x 2 Gauss quadrature.
+ *
+ * Array layouts (all FP64, all contiguous, caller-owned):
+ *   cell field   : N*N doubles, index j*N + i            (cell (i, j), j = y)
+ *   node vector  : 2*(N+1)^2 doubles, index 2*(j*(N+1) + i) + k, k = 0 (x), 1 (y)
+ *                  (node (i, j) at (i dx, j dx)); boundary entries are
+ *                  ignored on input and written as 0 on output.
+ *   dual state pi: 12*N*N doubles, index ((j*N + i)*4 + q)*3 + c, with
+ *                  quadrature point q = 2*qb + qa at local coordinates
+ *                  (g[qa], g[qb]), g = 1/2 -+ 1/(2 sqrt 3), and symmetric
+ *                  tensor component c = 0 (xx), 1 (yy), 2 (xy).
+ * Pointers are DEVICE pointers unless the function name ends in _host.  The
+ * library copies what it needs; it never keeps or frees a caller pointer.
+ * Every call is stream-ordered on the handle's stream; functions that return
+ * host-visible numbers synchronise that stream before returning.
+ *
+ * Errors.  Every function returns SVN_OK (0) or a negative SVN_ERR_* code and
+ * records a message readable with svn_last_error(h).  After SVN_ERR_CUDA the
+ * handle should be destroyed.  No function aborts the process.
+ */
+#ifndef SVN_H
+#define SVN_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SVN_MAX_NEWTON 200
+
+enum svn_status {
+  SVN_OK = 0,
+  SVN_ERR_ARG = -1,            /* invalid argument (sizes, NULL, constants) */
+  SVN_ERR_CUDA = -2,           /* a CUDA runtime call failed */
+  SVN_ERR_OOM = -3,            /* device allocation failed */
+  SVN_ERR_NONFINITE = -4,      /* NaN/Inf in inputs or in the residual norm */
+  SVN_ERR_NO_CONVERGENCE = -5, /* max_newton iterations without reaching tol */
+  SVN_ERR_LINESEARCH = -6,     /* max_halvings halvings without decrease of Phi */
+  SVN_ERR_KRYLOV = -7,         /* FGMRES breakdown or max_krylov reached */
+  SVN_ERR_TIMEOUT = -8,        /* a bounded device-side wait gave up */
+  SVN_ERR_STATE = -9           /* call order violated (e.g. step before forcing) */
+};
+
+enum svn_precision {
+  SVN_FP64 = 0,   /* every kernel in FP64 (the plain path) */
+  SVN_MIXED = 1   /* FP64 residual, energy, dual update, outer FGMRES and its
+                     operator; FP32 V-cycle on BF16-stored coefficients */
+};
+
+typedef struct svn_grid {
+  int N;          /* cells per side: even, 8 <= N <= 16384 */
+  double L;       /* side length [m] */
+} svn_grid;
+
+typedef struct svn_params {
+  /* physics (Table "tab:params"; P* in N/m^2, f_c explicit as in Section 3) */
+  double rho_ice, rho_a, rho_o, Ca, Co, f_c, Pstar, C, e, delta_min;
+  /* Newton (Section 5.1) */
+  int max_newton;           /* <= SVN_MAX_NEWTON */
+  int max_halvings;         /* backtracking halvings before SVN_ERR_LINESEARCH */
+  double ls_floor;          /* rounding floor of the Phi test, relative to sum |terms| */
+  /* Krylov + multigrid (Section 5.4) */
+  double krylov_rtol;       /* FGMRES stop: ||r|| <= krylov_rtol ||R(v_l)|| */
+  int restart;              /* FGMRES restart length */
+  int max_krylov;           /* FGMRES iteration cap per Newton step */
+  int precision;            /* enum svn_precision */
+  int cheb_degree;          /* Chebyshev-Jacobi smoothing steps per side (>= 1) */
+  double cheb_lo;           /* lower end of the Chebyshev interval, fraction of lmax */
+  int coarse_N;             /* coarsest multigrid level has coarse_N cells per side */
+  int eisenstat_walker;     /* 1: adapt krylov_rtol per Newton step (timed runs) */
+  int learned;              /* 1: try the learned initial guess (svn_learned_load) */
+} svn_params;
+
+typedef struct svn_stats {
+  int status;               /* same as the return code of svn_step */
+  int newton_iters;
+  int krylov_iters_total;
+  int halvings_total;
+  int learned_used;         /* the learned guess was tried */
+  int learned_fallback;     /* ... and rejected (larger residual than v_old) */
+  double res0;              /* ||R(v_old)||, the denominator of rel-res */
+  double res_final;
+  double rel_res_final;
+  double seconds;           /* wall time of the step on the host */
+  int krylov_per_newton[SVN_MAX_NEWTON];
+  double res_hist[SVN_MAX_NEWTON + 1];
+  double alpha_hist[SVN_MAX_NEWTON];
+} svn_stats;
+
+typedef struct svn_handle svn_handle;
+
+/* Fill *p with the paper's constants (P* = 27.5 kN/m^2, e = 2,
+ * Delta_min = 2e-9 1/s, f_c = 1.46e-4 1/s) and default solver settings. */
+int svn_default_params(svn_params* p);
+
+/* Create a solver for one grid on the current CUDA device.  cuda_stream is a
+ * cudaStream_t (NULL = legacy default stream).  Allocates all device
+ * workspace (the multigrid hierarchy, FGMRES basis, quadrature state). */
+int svn_create(const svn_grid* g, const svn_params* p, void* cuda_stream, svn_handle** out);
+int svn_destroy(svn_handle* h);
+const char* svn_last_error(const svn_handle* h);
+
+/* Inputs of one implicit step (Sections 2 and 3): cell thickness h [m] and
+ * concentration A at t_{n+1}, node wind v_a(t_{n+1}) and ocean v_o [m/s], and
+ * the previous velocity v^n.  Checks finiteness, h > 0 and 0 <= A <= 1
+ * (SVN_ERR_NONFINITE / SVN_ERR_ARG).  The step starts from v^n and
+ * pi = tau(v^n)/Delta(v^n). */
+int svn_set_forcing(svn_handle* h, const double* hcell, const double* A,
+                    const double* wind, const double* ocean, const double* v_old);
+int svn_set_forcing_host(svn_handle* h, const double* hcell, const double* A,
+                         const double* wind, const double* ocean, const double* v_old);
+
+/* One implicit step of length dt [s]: damped svN iterations until
+ * ||R(v_l)|| <= tol ||R(v^n)|| (Euclidean norm of the assembled residual over
+ * the free dofs).  out_v receives v^{n+1} (or the last iterate on error);
+ * stats (may be NULL) is filled in every case. */
+int svn_step(svn_handle* h, double dt, double tol, double* out_v, svn_stats* stats);
+int svn_step_host(svn_handle* h, double dt, double tol, double* out_v, svn_stats* stats);
+
+/* Current iterate v and dual state pi (checkpoint / warm restart). */
+int svn_get_state(svn_handle* h, double* v, double* pi);
+int svn_set_state(svn_handle* h, const double* v, const double* pi);
+
+/* ---- Hot-path components, one call per step of the method.  They use the
+ * forcing of the last svn_set_forcing and the given dt; all vectors are
+ * device node vectors of the handle's grid unless stated. ---- */
+
+/* Nonlinear residual R(v) = A(v, .) - F(.) (Eqs. "Av=F", "A", "F" with the
+ * stress in the tau-form of Eq. "sigma"), boundary rows 0, and its Euclidean
+ * norm (host double). */
+int svn_residual(svn_handle* h, double dt, const double* v, double* R, double* norm);
+
+/* Energy Phi(v + alpha_i dv) (Eq. "energy") for k <= 8 step lengths
+ * (host arrays alphas[k] -> phi[k]); *scale (may be NULL) receives the sum of
+ * |quadrature contributions| at alpha_0, the rounding scale of Phi. */
+int svn_energy(svn_handle* h, double dt, const double* v, const double* dv,
+               const double* alphas, int k, double* phi, double* scale);
+
+/* Build the svN linearisation at (v, pi): quadrature coefficients of
+ * Eq. "linearSVNewton" with Eq. "modification" and the ocean-drag derivative
+ * (Eq. "standardNewton2"), the level-0 stencil and the multigrid hierarchy.
+ * pi is a device dual state (layout above). */
+int svn_linearize(svn_handle* h, double dt, const double* v, const double* pi);
+
+/* y = K_level x with the operator of the last svn_linearize; level 0 is the
+ * FP64 svN operator, level l >= 1 the Galerkin coarse operator on the grid
+ * with N / 2^l cells (node vectors of that grid). */
+int svn_apply(svn_handle* h, int level, const double* x, double* y);
+
+/* z = M^{-1} r: one multigrid V-cycle of the last svn_linearize. */
+int svn_precondition(svn_handle* h, const double* r, double* z);
+
+/* Solve K x = b by preconditioned FGMRES to ||b - K x|| <= rtol ||b||
+ * (x starts at 0); *iters receives the iteration count. */
+int svn_krylov_solve(svn_handle* h, const double* b, double* x, double rtol, int* iters);
+
+/* Dual update pi <- pi + alpha pi~(v, dv, pi) (Eq. "tautilde" with the
+ * modification of Eq. "modification"), in place on the device array pi. */
+int svn_dual_update(svn_handle* h, double dt, const double* v, const double* dv,
+                    double alpha, double* pi);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SVN_H */

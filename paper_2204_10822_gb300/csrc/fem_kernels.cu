@@ -1,0 +1,612 @@
+// Per-cell FP64 kernels of the svN step: precomputation, the nonlinear
+// residual, the energy, the linearisation (quadrature coefficients, element
+// matrices, level-0 stencil) and the dual update.
+//
+// Every cell kernel evaluates the Q1 velocity and its gradient at the four
+// 2x2 Gauss points from the cell's four corner nodes.  Gradients are kept in
+// "hat" units (derivatives with respect to the local coordinates xi, eta in
+// [0, 1]); true gradients are hat / dx.
+#include "kernels.h"
+
+namespace svn {
+
+namespace {
+
+struct Corners {
+  double2 v00, v10, v01, v11;
+};
+
+__device__ __forceinline__ Corners load_corners(const double2* __restrict__ v, long long n00, int ld) {
+  Corners c;
+  c.v00 = v[n00];
+  c.v10 = v[n00 + 1];
+  c.v01 = v[n00 + ld];
+  c.v11 = v[n00 + ld + 1];
+  return c;
+}
+
+struct Qp {
+  double vx, vy;              // velocity
+  double gxx, gxy, gyx, gyy;  // hat gradient g[k][d] = d v_k / d xi_d
+};
+
+__device__ __forceinline__ Qp eval_qp(const Corners& c, double xi, double eta) {
+  Qp q;
+  const double n00 = (1.0 - xi) * (1.0 - eta), n10 = xi * (1.0 - eta);
+  const double n01 = (1.0 - xi) * eta, n11 = xi * eta;
+  q.vx = n00 * c.v00.x + n10 * c.v10.x + n01 * c.v01.x + n11 * c.v11.x;
+  q.vy = n00 * c.v00.y + n10 * c.v10.y + n01 * c.v01.y + n11 * c.v11.y;
+  q.gxx = (1.0 - eta) * (c.v10.x - c.v00.x) + eta * (c.v11.x - c.v01.x);
+  q.gyx = (1.0 - eta) * (c.v10.y - c.v00.y) + eta * (c.v11.y - c.v01.y);
+  q.gxy = (1.0 - xi) * (c.v01.x - c.v00.x) + xi * (c.v11.x - c.v10.x);
+  q.gyy = (1.0 - xi) * (c.v01.y - c.v00.y) + xi * (c.v11.y - c.v10.y);
+  return q;
+}
+
+// Shape functions and hat derivatives of corner c at (xi, eta).
+__device__ __forceinline__ void shape(int c, double xi, double eta, double& n, double& dxi, double& deta) {
+  const double a = (c & 1) ? xi : 1.0 - xi;
+  const double b = (c & 2) ? eta : 1.0 - eta;
+  n = a * b;
+  dxi = ((c & 1) ? 1.0 : -1.0) * b;
+  deta = ((c & 2) ? 1.0 : -1.0) * a;
+}
+
+__device__ __forceinline__ double qxi(int q) { return (q & 1) ? GQ1 : GQ0; }
+__device__ __forceinline__ double qeta(int q) { return (q & 2) ? GQ1 : GQ0; }
+
+// hat tau (Voigt-free components) from the hat gradient:
+// tau = e^-1 eps' + tr(eps) I / 2  ->  txx = ta gxx + tb gyy, tyy = tb gxx + ta gyy,
+// txy = tc (gxy + gyx).
+__device__ __forceinline__ void tau_hat(const Phys& ph, const Qp& q, double& txx, double& tyy, double& txy) {
+  txx = ph.ta * q.gxx + ph.tb * q.gyy;
+  tyy = ph.tb * q.gxx + ph.ta * q.gyy;
+  txy = ph.tc * (q.gxy + q.gyx);
+}
+
+__device__ __forceinline__ bool interior(int i, int j, int N) { return i >= 1 && j >= 1 && i <= N - 1 && j <= N - 1; }
+
+// ---- a1: precomputation ---------------------------------------------------------
+__global__ void k_precompute(Layout g, double dt, PhysConst pc, const double* __restrict__ hcell,
+                             const double* __restrict__ A, const double* __restrict__ wind,
+                             const double* __restrict__ ocean, const double* __restrict__ vold,
+                             double* __restrict__ P, double* __restrict__ rhoH, double* __restrict__ fq,
+                             double* __restrict__ voq) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= g.N || j >= g.N) return;
+  const int n1 = g.N + 1;
+  const long long cell = (long long)j * g.ld + i;
+  const double h = hcell[(long long)j * g.N + i];
+  const double a = A[(long long)j * g.N + i];
+  const double Pc = pc.Pstar * h * exp(-pc.C * (1.0 - a));   // Eq. "ice-strength"
+  const double rh = pc.rho_ice * h;
+  P[cell] = Pc;
+  rhoH[cell] = rh;
+  // corner values (unpadded caller layout); v^n is zero on the boundary
+  double wx[4], wy[4], ox[4], oy[4], nx[4], ny[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const int ii = i + (c & 1), jj = j + (c >> 1);
+    const long long k = 2 * ((long long)jj * n1 + ii);
+    wx[c] = wind[k];
+    wy[c] = wind[k + 1];
+    ox[c] = ocean[k];
+    oy[c] = ocean[k + 1];
+    const bool bnd = ii == 0 || jj == 0 || ii == g.N || jj == g.N;
+    nx[c] = bnd ? 0.0 : vold[k];
+    ny[c] = bnd ? 0.0 : vold[k + 1];
+  }
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double xi = qxi(q), eta = qeta(q);
+    double s[4];
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      double n, d1, d2;
+      shape(c, xi, eta, n, d1, d2);
+      s[c] = n;
+    }
+    double vax = 0, vay = 0, vox = 0, voy = 0, vnx = 0, vny = 0;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      vax += s[c] * wx[c];
+      vay += s[c] * wy[c];
+      vox += s[c] * ox[c];
+      voy += s[c] * oy[c];
+      vnx += s[c] * nx[c];
+      vny += s[c] * ny[c];
+    }
+    // tau_atm = Ca rho_a |v_a| v_a (Eq. "force"); explicit Coriolis
+    // rho H f e_r x (v^n - v_o), e_r x w = (-w_y, w_x) (Eq. "F")
+    const double sa = pc.Ca * pc.rho_a * sqrt(vax * vax + vay * vay);
+    const double dwx = vnx - vox, dwy = vny - voy;
+    const double corx = -rh * pc.f_c * dwy, cory = rh * pc.f_c * dwx;
+    // constant part of the residual source: -rho H v^n + dt cor - dt tau_atm
+    fq[(2 * q) * g.plane + cell] = -rh * vnx + dt * corx - dt * sa * vax;
+    fq[(2 * q + 1) * g.plane + cell] = -rh * vny + dt * cory - dt * sa * vay;
+    voq[(2 * q) * g.plane + cell] = vox;
+    voq[(2 * q + 1) * g.plane + cell] = voy;
+  }
+}
+
+// pi_0 = tau(v) / Delta(v) at every quadrature point (Eq. "pi").
+__global__ void k_pi_init(Layout g, Phys ph, const double2* __restrict__ v, double* __restrict__ pi) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= g.N || j >= g.N) return;
+  const long long cell = (long long)j * g.ld + i;
+  const Corners c = load_corners(v, cell, g.ld);
+  const double idx = 1.0 / ph.dx;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const Qp p = eval_qp(c, qxi(q), qeta(q));
+    double txx, tyy, txy;
+    tau_hat(ph, p, txx, tyy, txy);
+    txx *= idx; tyy *= idx; txy *= idx;
+    const double inv = rsqrt(ph.dmin2 + 2.0 * (txx * txx + tyy * tyy + 2.0 * txy * txy));
+    pi[(3 * q + 0) * g.plane + cell] = txx * inv;
+    pi[(3 * q + 1) * g.plane + cell] = tyy * inv;
+    pi[(3 * q + 2) * g.plane + cell] = txy * inv;
+  }
+}
+
+// ---- a2: nonlinear residual ------------------------------------------------------
+// Per cell: the 8 nodal contributions sum_q w [N_c s_q] + VP term, written to
+// 8 planes (corner c, component k) of `eb`.
+__global__ void k_residual_cells(Layout g, Phys ph, const double2* __restrict__ v, const double* __restrict__ P,
+                                 const double* __restrict__ rhoH, const double* __restrict__ fq,
+                                 const double* __restrict__ voq, double* __restrict__ eb) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= g.N || j >= g.N) return;
+  const long long cell = (long long)j * g.ld + i;
+  const Corners c = load_corners(v, cell, g.ld);
+  const double Pdt = ph.dt * P[cell];
+  const double rh = rhoH[cell];
+  const double idx = 1.0 / ph.dx;
+  const double vpw = 0.25 * ph.dx;   // w / dx
+  double rx[4] = {0, 0, 0, 0}, ry[4] = {0, 0, 0, 0};
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double xi = qxi(q), eta = qeta(q);
+    const Qp p = eval_qp(c, xi, eta);
+    double txx, tyy, txy;
+    tau_hat(ph, p, txx, tyy, txy);
+    const double tt = (txx * txx + tyy * tyy + 2.0 * txy * txy) * idx * idx;
+    const double inv = rsqrt(ph.dmin2 + 2.0 * tt);            // 1 / Delta
+    const double sfac = Pdt * inv * idx;                       // dt P / Delta / dx
+    const double Sxx = sfac * txx, Syy = sfac * tyy, Sxy = sfac * txy;
+    const double Fxx = ph.ta * Sxx + ph.tb * Syy - 0.5 * Pdt;
+    const double Fyy = ph.tb * Sxx + ph.ta * Syy - 0.5 * Pdt;
+    const double Fxy = 2.0 * ph.tc * Sxy;
+    // source: rho H v + (-rho H v^n + dt cor - dt tau_atm) - dt Co rho_o |w| w
+    const double wx = voq[(2 * q) * g.plane + cell] - p.vx;
+    const double wy = voq[(2 * q + 1) * g.plane + cell] - p.vy;
+    const double dr = ph.dt * ph.cdrag * sqrt(wx * wx + wy * wy);
+    const double sx = ph.w * (rh * p.vx + fq[(2 * q) * g.plane + cell] - dr * wx);
+    const double sy = ph.w * (rh * p.vy + fq[(2 * q + 1) * g.plane + cell] - dr * wy);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      double n, dxi, deta;
+      shape(k, xi, eta, n, dxi, deta);
+      rx[k] += n * sx + vpw * (Fxx * dxi + Fxy * deta);
+      ry[k] += n * sy + vpw * (Fxy * dxi + Fyy * deta);
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    eb[(2 * k) * g.plane + cell] = rx[k];
+    eb[(2 * k + 1) * g.plane + cell] = ry[k];
+  }
+}
+
+// Gather cell contributions into nodes; boundary rows are 0.  Per-block
+// partial sums of |R|^2 go to `partial`.
+__global__ void k_residual_nodes(Layout g, const double* __restrict__ eb, double2* __restrict__ R,
+                                 double* __restrict__ partial) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  double s = 0.0;
+  if (i <= g.N && j <= g.N) {
+    const long long n = (long long)j * g.ld + i;
+    double2 r = make_double2(0.0, 0.0);
+    if (interior(i, j, g.N)) {
+      // cells (i-1, j-1): corner 3; (i, j-1): corner 2; (i-1, j): corner 1; (i, j): corner 0
+      const long long c3 = n - g.ld - 1, c2 = n - g.ld, c1 = n - 1, c0 = n;
+      r.x = eb[6 * g.plane + c3] + eb[4 * g.plane + c2] + eb[2 * g.plane + c1] + eb[0 * g.plane + c0];
+      r.y = eb[7 * g.plane + c3] + eb[5 * g.plane + c2] + eb[3 * g.plane + c1] + eb[1 * g.plane + c0];
+      s = r.x * r.x + r.y * r.y;
+    }
+    R[n] = r;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = s;
+}
+
+// ---- a8: energy for k step lengths --------------------------------------------------
+// Phi_h(v + alpha dv) = sum over cells and quadrature points of
+//   w [ rho H |u|^2 / 2 + fq . u + dt P/2 (Delta - tr eps) + dt Co rho_o |v_o - u|^3 / 3 ]
+// with fq . u = -rho H v^n . u + dt cor . u - dt tau_atm . u.  Compensated sums.
+__global__ void k_energy_cells(Layout g, Phys ph, int k, AlphaSet al, const double2* __restrict__ v,
+                               const double2* __restrict__ dv, const double* __restrict__ P,
+                               const double* __restrict__ rhoH, const double* __restrict__ fq,
+                               const double* __restrict__ voq, double* __restrict__ partial, int nblocks) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  DD acc[MAX_ALPHA];
+  double asum = 0.0;
+#pragma unroll
+  for (int a = 0; a < MAX_ALPHA; ++a) acc[a] = DD{0.0, 0.0};
+  if (i < g.N && j < g.N) {
+    const long long cell = (long long)j * g.ld + i;
+    const Corners c0 = load_corners(v, cell, g.ld);
+    const Corners d0 = load_corners(dv, cell, g.ld);
+    const double Ph = 0.5 * ph.dt * P[cell];
+    const double rh = rhoH[cell];
+    const double idx = 1.0 / ph.dx;
+    for (int a = 0; a < k; ++a) {
+      const double al0 = al.a[a];
+      Corners c;
+      c.v00 = make_double2(c0.v00.x + al0 * d0.v00.x, c0.v00.y + al0 * d0.v00.y);
+      c.v10 = make_double2(c0.v10.x + al0 * d0.v10.x, c0.v10.y + al0 * d0.v10.y);
+      c.v01 = make_double2(c0.v01.x + al0 * d0.v01.x, c0.v01.y + al0 * d0.v01.y);
+      c.v11 = make_double2(c0.v11.x + al0 * d0.v11.x, c0.v11.y + al0 * d0.v11.y);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const Qp p = eval_qp(c, qxi(q), qeta(q));
+        double txx, tyy, txy;
+        tau_hat(ph, p, txx, tyy, txy);
+        const double tt = (txx * txx + tyy * tyy + 2.0 * txy * txy) * idx * idx;
+        const double Dl = sqrt(ph.dmin2 + 2.0 * tt);
+        const double tr = (p.gxx + p.gyy) * idx;
+        const double wx = voq[(2 * q) * g.plane + cell] - p.vx;
+        const double wy = voq[(2 * q + 1) * g.plane + cell] - p.vy;
+        const double nw = sqrt(wx * wx + wy * wy);
+        const double t1 = 0.5 * rh * (p.vx * p.vx + p.vy * p.vy);
+        const double t2 = fq[(2 * q) * g.plane + cell] * p.vx + fq[(2 * q + 1) * g.plane + cell] * p.vy;
+        const double t3 = Ph * (Dl - tr);
+        const double t4 = ph.dt * ph.cdrag * nw * nw * nw * (1.0 / 3.0);
+        acc[a].add(ph.w * t1);
+        acc[a].add(ph.w * t2);
+        acc[a].add(ph.w * t3);
+        acc[a].add(ph.w * t4);
+        if (a == 0) asum += ph.w * (fabs(t1) + fabs(t2) + fabs(t3) + fabs(t4));
+      }
+    }
+  }
+  // block reduction of the (hi, lo) pairs, then write per-block partials:
+  // layout partial[(2 a) * nblocks + bid] = hi, [(2 a + 1) * nblocks + bid] = lo,
+  // partial[(2 MAX_ALPHA) * nblocks + bid] = sum |terms|
+  __shared__ double sh_hi[256], sh_lo[256];
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nt = blockDim.x * blockDim.y;
+  for (int a = 0; a < k; ++a) {
+    sh_hi[tid] = acc[a].hi;
+    sh_lo[tid] = acc[a].lo;
+    __syncthreads();
+    for (int s = nt / 2; s > 0; s >>= 1) {
+      if (tid < s) {
+        DD x{sh_hi[tid], sh_lo[tid]};
+        x.add(DD{sh_hi[tid + s], sh_lo[tid + s]});
+        sh_hi[tid] = x.hi;
+        sh_lo[tid] = x.lo;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) {
+      partial[(2 * a) * nblocks + bid] = sh_hi[0];
+      partial[(2 * a + 1) * nblocks + bid] = sh_lo[0];
+    }
+    __syncthreads();
+  }
+  asum = block_sum(asum);
+  if (tid == 0) partial[(2 * MAX_ALPHA) * nblocks + bid] = asum;
+}
+
+// Final compensated reduction of the energy partials: out[a] = Phi, out[MAX_ALPHA] = scale.
+__global__ void k_energy_final(int k, const double* __restrict__ partial, int nblocks, double* __restrict__ out) {
+  __shared__ double sh_hi[1024], sh_lo[1024];
+  const int tid = threadIdx.x;
+  for (int a = 0; a < k; ++a) {
+    DD acc{0.0, 0.0};
+    for (int b = tid; b < nblocks; b += blockDim.x) {
+      acc.add(DD{partial[(2 * a) * nblocks + b], partial[(2 * a + 1) * nblocks + b]});
+    }
+    sh_hi[tid] = acc.hi;
+    sh_lo[tid] = acc.lo;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+      if (tid < s) {
+        DD x{sh_hi[tid], sh_lo[tid]};
+        x.add(DD{sh_hi[tid + s], sh_lo[tid + s]});
+        sh_hi[tid] = x.hi;
+        sh_lo[tid] = x.lo;
+      }
+      __syncthreads();
+    }
+    if (tid == 0) out[a] = sh_hi[0] + sh_lo[0];
+    __syncthreads();
+  }
+  double s = 0.0;
+  for (int b = tid; b < nblocks; b += blockDim.x) s += partial[(2 * MAX_ALPHA) * nblocks + b];
+  s = block_sum(s);
+  if (tid == 0) out[MAX_ALPHA] = s;
+}
+
+// ---- a3/a4: linearisation -------------------------------------------------------------
+// Per cell: at every quadrature point the svN coefficient (Eq. "linearSVNewton"
+// with Eq. "modification", Voigt form)
+//   C = dt [ (P/Delta) I - P/(Delta^2 m) (t p^T + p t^T) ],  m = max(1, sqrt(2 pi:pi)),
+// the mass tensor M = rho H I + dt Co rho_o (|w| I + w w^T / |w|) (Eq.
+// "standardNewton2"; the rank-one term is dropped for |w| < 1e-14 m/s), and
+// the element matrix K_e = sum_q w (N^T M N + B^T C B), upper triangle.
+template <typename TE>
+__global__ void k_element_matrices(Layout g, Phys ph, const double2* __restrict__ v,
+                                   const double* __restrict__ pi, const double* __restrict__ P,
+                                   const double* __restrict__ rhoH, const double* __restrict__ voq,
+                                   TE* __restrict__ ke, float* __restrict__ qcoef) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= g.N || j >= g.N) return;
+  const long long cell = (long long)j * g.ld + i;
+  const Corners c = load_corners(v, cell, g.ld);
+  const double Pc = P[cell];
+  const double rh = rhoH[cell];
+  const double idx = 1.0 / ph.dx;
+  const double sq2 = 1.4142135623730950488;
+  double K[NELEM];
+#pragma unroll
+  for (int e = 0; e < NELEM; ++e) K[e] = 0.0;
+#pragma unroll 1
+  for (int q = 0; q < 4; ++q) {
+    const double xi = qxi(q), eta = qeta(q);
+    const Qp p = eval_qp(c, xi, eta);
+    double txx, tyy, txy;
+    tau_hat(ph, p, txx, tyy, txy);
+    const double t0 = txx * idx, t1 = tyy * idx, t2 = sq2 * txy * idx;   // Voigt tau
+    const double d2 = ph.dmin2 + 2.0 * (t0 * t0 + t1 * t1 + t2 * t2);
+    const double inv = rsqrt(d2);
+    const double p0 = pi[(3 * q + 0) * g.plane + cell];
+    const double p1 = pi[(3 * q + 1) * g.plane + cell];
+    const double p2 = sq2 * pi[(3 * q + 2) * g.plane + cell];
+    const double pp = p0 * p0 + p1 * p1 + p2 * p2;
+    const double m = fmax(1.0, sqrt(2.0 * pp));                        // FP64 branch
+    const double a = ph.dt * Pc * inv;                                 // dt P / Delta
+    const double b = ph.dt * Pc * inv * inv / m;                       // dt P / (Delta^2 m)
+    // C = a I - b (t p^T + p t^T), symmetric
+    const double C00 = a - 2.0 * b * t0 * p0, C11 = a - 2.0 * b * t1 * p1, C22 = a - 2.0 * b * t2 * p2;
+    const double C01 = -b * (t0 * p1 + p0 * t1), C02 = -b * (t0 * p2 + p0 * t2), C12 = -b * (t1 * p2 + p1 * t2);
+    // mass tensor
+    const double wx = voq[(2 * q) * g.plane + cell] - p.vx;
+    const double wy = voq[(2 * q + 1) * g.plane + cell] - p.vy;
+    const double nw2 = wx * wx + wy * wy;
+    const double nw = sqrt(nw2);
+    const double od = ph.dt * ph.cdrag;
+    double Mxx = rh + od * nw, Myy = rh + od * nw, Mxy = 0.0;
+    if (nw >= 1e-14) {
+      const double r1 = od / nw;
+      Mxx += r1 * wx * wx;
+      Myy += r1 * wy * wy;
+      Mxy = r1 * wx * wy;
+    }
+    if (qcoef != nullptr) {
+      float* qc = qcoef + (long long)(NQCOEF * q) * g.plane + cell;
+      qc[0 * g.plane] = (float)C00; qc[1 * g.plane] = (float)C11; qc[2 * g.plane] = (float)C22;
+      qc[3 * g.plane] = (float)C01; qc[4 * g.plane] = (float)C02; qc[5 * g.plane] = (float)C12;
+      qc[6 * g.plane] = (float)Mxx; qc[7 * g.plane] = (float)Myy; qc[8 * g.plane] = (float)Mxy;
+    }
+    // basis vectors: value n[c], hat tau Voigt of N_c e_x and N_c e_y
+    double n[4], bx[4][3], by[4][3];
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+      double dxi, deta;
+      shape(cc, xi, eta, n[cc], dxi, deta);
+      bx[cc][0] = ph.ta * dxi; bx[cc][1] = ph.tb * dxi; bx[cc][2] = sq2 * ph.tc * deta;
+      by[cc][0] = ph.tb * deta; by[cc][1] = ph.ta * deta; by[cc][2] = sq2 * ph.tc * dxi;
+    }
+    // stiffness weight: w / dx^2 = 1/4; mass weight w
+    double Bv[8][3], CB[8][3];
+#pragma unroll
+    for (int cc = 0; cc < 4; ++cc) {
+#pragma unroll
+      for (int s = 0; s < 3; ++s) {
+        Bv[2 * cc][s] = bx[cc][s];
+        Bv[2 * cc + 1][s] = by[cc][s];
+      }
+    }
+#pragma unroll
+    for (int d = 0; d < 8; ++d) {
+      CB[d][0] = 0.25 * (C00 * Bv[d][0] + C01 * Bv[d][1] + C02 * Bv[d][2]);
+      CB[d][1] = 0.25 * (C01 * Bv[d][0] + C11 * Bv[d][1] + C12 * Bv[d][2]);
+      CB[d][2] = 0.25 * (C02 * Bv[d][0] + C12 * Bv[d][1] + C22 * Bv[d][2]);
+    }
+#pragma unroll
+    for (int r = 0; r < 8; ++r) {
+#pragma unroll
+      for (int s = r; s < 8; ++s) {
+        double val = Bv[r][0] * CB[s][0] + Bv[r][1] * CB[s][1] + Bv[r][2] * CB[s][2];
+        const int kr = r & 1, ks = s & 1;
+        const double mkl = (kr == ks) ? (kr == 0 ? Mxx : Myy) : Mxy;
+        val += ph.w * n[r >> 1] * n[s >> 1] * mkl;
+        K[elem_index(r, s)] += val;
+      }
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < NELEM; ++e) ke[e * g.plane + cell] = (TE)K[e];
+}
+
+// Element-matrix entry (r, s) of cell `cell`, either triangle.
+template <typename TE>
+__device__ __forceinline__ double kel(const TE* __restrict__ ke, long long plane, long long cell, int r, int s) {
+  return (double)ke[(long long)(r <= s ? elem_index(r, s) : elem_index(s, r)) * plane + cell];
+}
+
+// Gather the level-0 stencil at interior nodes from the element matrices.
+template <typename TE, typename TS>
+__global__ void k_stencil_from_elements(Layout g, const TE* __restrict__ ke, TS* __restrict__ st) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (!interior(i, j, g.N)) return;
+  const long long n = (long long)j * g.ld + i;
+  const long long pl = g.plane;
+  // cells around node n, with the node's corner index in each
+  const long long cl[4] = {n, n - 1, n - g.ld, n - g.ld - 1};
+  const int cp[4] = {0, 1, 2, 3};
+  double dxx = 0, dxy = 0, dyy = 0;
+#pragma unroll
+  for (int t = 0; t < 4; ++t) {
+    const int c = cp[t];
+    dxx += kel(ke, pl, cl[t], 2 * c, 2 * c);
+    dxy += kel(ke, pl, cl[t], 2 * c, 2 * c + 1);
+    dyy += kel(ke, pl, cl[t], 2 * c + 1, 2 * c + 1);
+  }
+  st[(S_D + 0) * pl + n] = (TS)dxx;
+  st[(S_D + 1) * pl + n] = (TS)dxy;
+  st[(S_D + 2) * pl + n] = (TS)dyy;
+  // off-diagonal blocks: (cell, corner of p, corner of q) pairs
+  auto blk = [&](int slot, int npairs, const long long* cells, const int* cpp, const int* cqq) {
+    double b[4] = {0, 0, 0, 0};
+    for (int t = 0; t < npairs; ++t) {
+#pragma unroll
+      for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int l = 0; l < 2; ++l) b[2 * k + l] += kel(ke, pl, cells[t], 2 * cpp[t] + k, 2 * cqq[t] + l);
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) st[(slot + e) * pl + n] = (TS)b[e];
+  };
+  {  // E: cells (i, j-1) [p=2, q=3] and (i, j) [p=0, q=1]
+    const long long cs[2] = {n - g.ld, n};
+    const int a[2] = {2, 0}, b[2] = {3, 1};
+    blk(S_E, 2, cs, a, b);
+  }
+  {  // N: cells (i-1, j) [p=1, q=3] and (i, j) [p=0, q=2]
+    const long long cs[2] = {n - 1, n};
+    const int a[2] = {1, 0}, b[2] = {3, 2};
+    blk(S_N, 2, cs, a, b);
+  }
+  {  // NE: cell (i, j) [p=0, q=3]
+    const long long cs[1] = {n};
+    const int a[1] = {0}, b[1] = {3};
+    blk(S_NE, 1, cs, a, b);
+  }
+  {  // NW: cell (i-1, j) [p=1, q=2]
+    const long long cs[1] = {n - 1};
+    const int a[1] = {1}, b[1] = {2};
+    blk(S_NW, 1, cs, a, b);
+  }
+}
+
+// ---- a9: dual update ------------------------------------------------------------------
+// pi <- pi + alpha pi~, pi~ = -pi + t/Delta + t~/Delta - [(t.t~) p + (p.t~) t] / (Delta^2 m)
+// in Voigt form (Eq. "tautilde" with Eq. "modification"), t = tau(v), t~ = tau(dv).
+__global__ void k_dual_update(Layout g, Phys ph, double alpha, const double2* __restrict__ v,
+                              const double2* __restrict__ dv, double* __restrict__ pi) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= g.N || j >= g.N) return;
+  const long long cell = (long long)j * g.ld + i;
+  const Corners c = load_corners(v, cell, g.ld);
+  const Corners d = load_corners(dv, cell, g.ld);
+  const double idx = 1.0 / ph.dx;
+  const double sq2 = 1.4142135623730950488;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const double xi = qxi(q), eta = qeta(q);
+    const Qp p = eval_qp(c, xi, eta);
+    const Qp pd = eval_qp(d, xi, eta);
+    double txx, tyy, txy, sxx, syy, sxy;
+    tau_hat(ph, p, txx, tyy, txy);
+    tau_hat(ph, pd, sxx, syy, sxy);
+    const double t0 = txx * idx, t1 = tyy * idx, t2 = sq2 * txy * idx;
+    const double s0 = sxx * idx, s1 = syy * idx, s2 = sq2 * sxy * idx;
+    const double inv = rsqrt(ph.dmin2 + 2.0 * (t0 * t0 + t1 * t1 + t2 * t2));
+    double* pq = pi + (long long)(3 * q) * g.plane + cell;
+    const double p0 = pq[0], p1 = pq[g.plane], p2 = sq2 * pq[2 * g.plane];
+    const double m = fmax(1.0, sqrt(2.0 * (p0 * p0 + p1 * p1 + p2 * p2)));
+    const double ts = t0 * s0 + t1 * s1 + t2 * s2;
+    const double ps = p0 * s0 + p1 * s1 + p2 * s2;
+    const double f = inv * inv / m;
+    const double n0 = -p0 + (t0 + s0) * inv - (ts * p0 + ps * t0) * f;
+    const double n1 = -p1 + (t1 + s1) * inv - (ts * p1 + ps * t1) * f;
+    const double n2 = -p2 + (t2 + s2) * inv - (ts * p2 + ps * t2) * f;
+    pq[0] = p0 + alpha * n0;
+    pq[g.plane] = p1 + alpha * n1;
+    pq[2 * g.plane] = (p2 + alpha * n2) * (1.0 / sq2);
+  }
+}
+
+inline dim3 cell_grid(const Layout& g, dim3 blk) {
+  return dim3((g.N + blk.x - 1) / blk.x, (g.N + blk.y - 1) / blk.y);
+}
+inline dim3 node_grid(const Layout& g, dim3 blk) {
+  return dim3((g.n1 + blk.x - 1) / blk.x, (g.n1 + blk.y - 1) / blk.y);
+}
+
+}  // namespace
+
+// ---- launchers ---------------------------------------------------------------------
+const dim3 kCellBlock(32, 4);
+const dim3 kNodeBlock(32, 8);
+
+void launch_precompute(cudaStream_t s, const Layout& g, double dt, const PhysConst& pc, const double* hcell,
+                       const double* A, const double* wind, const double* ocean, const double* vold, double* P,
+                       double* rhoH, double* fq, double* voq) {
+  k_precompute<<<cell_grid(g, kCellBlock), kCellBlock, 0, s>>>(g, dt, pc, hcell, A, wind, ocean, vold, P, rhoH,
+                                                              fq, voq);
+}
+
+void launch_pi_init(cudaStream_t s, const Layout& g, const Phys& ph, const double2* v, double* pi) {
+  k_pi_init<<<cell_grid(g, kCellBlock), kCellBlock, 0, s>>>(g, ph, v, pi);
+}
+
+int residual_partials(const Layout& g) {
+  dim3 gr = node_grid(g, kNodeBlock);
+  return gr.x * gr.y;
+}
+
+void launch_residual(cudaStream_t s, const Layout& g, const Phys& ph, const double2* v, const double* P,
+                     const double* rhoH, const double* fq, const double* voq, double* eb, double2* R,
+                     double* partial) {
+  k_residual_cells<<<cell_grid(g, kCellBlock), kCellBlock, 0, s>>>(g, ph, v, P, rhoH, fq, voq, eb);
+  k_residual_nodes<<<node_grid(g, kNodeBlock), kNodeBlock, 0, s>>>(g, eb, R, partial);
+}
+
+int energy_partials(const Layout& g) {
+  dim3 gr = cell_grid(g, kCellBlock);
+  return gr.x * gr.y;
+}
+
+void launch_energy(cudaStream_t s, const Layout& g, const Phys& ph, int k, const AlphaSet& al, const double2* v,
+                   const double2* dv, const double* P, const double* rhoH, const double* fq, const double* voq,
+                   double* partial, double* out) {
+  dim3 gr = cell_grid(g, kCellBlock);
+  const int nb = gr.x * gr.y;
+  k_energy_cells<<<gr, kCellBlock, 0, s>>>(g, ph, k, al, v, dv, P, rhoH, fq, voq, partial, nb);
+  k_energy_final<<<1, 1024, 0, s>>>(k, partial, nb, out);
+}
+
+template <typename TE>
+void launch_element_matrices(cudaStream_t s, const Layout& g, const Phys& ph, const double2* v, const double* pi,
+                             const double* P, const double* rhoH, const double* voq, TE* ke, float* qcoef) {
+  k_element_matrices<TE><<<cell_grid(g, kCellBlock), kCellBlock, 0, s>>>(g, ph, v, pi, P, rhoH, voq, ke, qcoef);
+}
+template void launch_element_matrices<double>(cudaStream_t, const Layout&, const Phys&, const double2*,
+                                              const double*, const double*, const double*, const double*,
+                                              double*, float*);
+
+template <typename TE, typename TS>
+void launch_stencil_from_elements(cudaStream_t s, const Layout& g, const TE* ke, TS* st) {
+  k_stencil_from_elements<TE, TS><<<node_grid(g, kNodeBlock), kNodeBlock, 0, s>>>(g, ke, st);
+}
+template void launch_stencil_from_elements<double, double>(cudaStream_t, const Layout&, const double*, double*);
+
+void launch_dual_update(cudaStream_t s, const Layout& g, const Phys& ph, double alpha, const double2* v,
+                        const double2* dv, double* pi) {
+  k_dual_update<<<cell_grid(g, kCellBlock), kCellBlock, 0, s>>>(g, ph, alpha, v, dv, pi);
+}
+
+}  // namespace svn

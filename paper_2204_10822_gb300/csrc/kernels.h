@@ -1,0 +1,103 @@
+// Host-side launchers of the svN CUDA kernels (all stream-ordered).
+#pragma once
+
+#include "svn_internal.cuh"
+
+namespace svn {
+
+constexpr int MAX_ALPHA = 8;
+struct AlphaSet {
+  double a[MAX_ALPHA];
+};
+
+struct PhysConst {
+  double rho_ice, rho_a, rho_o, Ca, Co, f_c, Pstar, C, e, delta_min;
+};
+
+// ---- cell kernels (fem_kernels.cu) ----
+void launch_precompute(cudaStream_t s, const Layout& g, double dt, const PhysConst& pc, const double* hcell,
+                       const double* A, const double* wind, const double* ocean, const double* vold, double* P,
+                       double* rhoH, double* fq, double* voq);
+void launch_pi_init(cudaStream_t s, const Layout& g, const Phys& ph, const double2* v, double* pi);
+int residual_partials(const Layout& g);
+void launch_residual(cudaStream_t s, const Layout& g, const Phys& ph, const double2* v, const double* P,
+                     const double* rhoH, const double* fq, const double* voq, double* eb, double2* R,
+                     double* partial);
+int energy_partials(const Layout& g);
+void launch_energy(cudaStream_t s, const Layout& g, const Phys& ph, int k, const AlphaSet& al, const double2* v,
+                   const double2* dv, const double* P, const double* rhoH, const double* fq, const double* voq,
+                   double* partial, double* out);
+template <typename TE>
+void launch_element_matrices(cudaStream_t s, const Layout& g, const Phys& ph, const double2* v, const double* pi,
+                             const double* P, const double* rhoH, const double* voq, TE* ke, float* qcoef);
+template <typename TE, typename TS>
+void launch_stencil_from_elements(cudaStream_t s, const Layout& g, const TE* ke, TS* st);
+void launch_dual_update(cudaStream_t s, const Layout& g, const Phys& ph, double alpha, const double2* v,
+                        const double2* dv, double* pi);
+
+// ---- stencil / multigrid kernels (mg_kernels.cu) ----
+// y = A x on interior nodes (0 elsewhere); TA accumulates.
+template <typename TS, typename TX, typename TY, typename TA>
+void launch_apply(cudaStream_t s, const Layout& g, const TS* st, const TX* x, TY* y);
+// r = b - A x
+template <typename TS, typename TV>
+void launch_residual_stencil(cudaStream_t s, const Layout& g, const TS* st, const TV* x, const TV* b, TV* r);
+// Block-Jacobi inverse (3 planes: xx, xy, yy) and per-block Gershgorin maxima.
+template <typename TS, typename TD>
+int launch_dinv_gershgorin(cudaStream_t s, const Layout& g, const TS* st, TD* dinv, double* partial);
+void launch_max_final(cudaStream_t s, const double* partial, int n, double* out);
+// Chebyshev smoothing (Saad Alg. 12.1 on D^-1 A over [lo lmax, lmax]).
+template <typename TS, typename TD, typename TV>
+void launch_cheb_zero_start(cudaStream_t s, const Layout& g, const TD* dinv, const double* lmax, double lo,
+                            const TV* b, TV* x, TV* d);
+template <typename TS, typename TD, typename TV>
+void launch_cheb_sweep(cudaStream_t s, const Layout& g, const TS* st, const TD* dinv, const double* lmax,
+                       double lo, int step, const TV* xin, TV* xout, TV* d, const TV* b);
+template <typename TV>
+void launch_restrict(cudaStream_t s, const Layout& gf, const Layout& gc, const TV* rf, TV* bc);
+template <typename TV>
+void launch_prolong_add(cudaStream_t s, const Layout& gf, const Layout& gc, const TV* xc, TV* xf);
+template <typename TF, typename TC>
+void launch_rap(cudaStream_t s, const Layout& gf, const Layout& gc, const TF* stf, TC* stc);
+template <typename TS>
+void launch_coarse_dense(cudaStream_t s, const Layout& g, const TS* st, double* dense);
+void launch_cholesky_inverse(cudaStream_t s, int n, double* a, double* inv, int* info);
+template <typename TV>
+void launch_coarse_solve(cudaStream_t s, const Layout& g, int n, const double* inv, const TV* b, TV* x);
+template <typename TA, typename TB>
+void launch_convert_stencil(cudaStream_t s, const Layout& g, const TA* a, TB* b);
+
+// ---- vector / Krylov kernels (krylov_kernels.cu) ----
+int reduce_blocks(long long n);
+void launch_sum_final(cudaStream_t s, const double* partial, int n, double* out);
+// node vectors are double2 / float2 arrays of g.plane entries
+void launch_unpack_nodes(cudaStream_t s, const Layout& g, const double* src, double2* dst);
+void launch_pack_nodes(cudaStream_t s, const Layout& g, const double2* src, double* dst);
+void launch_unpack_pi(cudaStream_t s, const Layout& g, const double* src, double* pi);
+void launch_pack_pi(cudaStream_t s, const Layout& g, const double* pi, double* dst);
+void launch_norm2_partial(cudaStream_t s, const Layout& g, const double2* x, double* partial);
+void launch_scale_copy(cudaStream_t s, const Layout& g, const double2* x, const double* num, const double* den,
+                       double2* y);   // y = x * (*num / *den)
+void launch_axpy(cudaStream_t s, const Layout& g, double a, const double2* x, double2* y);   // y += a x
+void launch_axpby_to(cudaStream_t s, const Layout& g, const double2* x, double a, const double2* d,
+                     double2* y);   // y = x + a d
+void launch_scale_to(cudaStream_t s, const Layout& g, double a, const double2* x, double2* y);   // y = a x
+void launch_validate(cudaStream_t s, long long ncell, long long nvec, const double* h, const double* A,
+                     const double* wind, const double* ocean, const double* vold, int* counts);
+void launch_neg_copy(cudaStream_t s, const Layout& g, const double2* x, double2* y);
+void launch_cast_d2f(cudaStream_t s, const Layout& g, const double2* x, float2* y);
+void launch_cast_f2d(cudaStream_t s, const Layout& g, const float2* x, double2* y);
+// Arnoldi: h[i] (i < m) partial dots of V_i with w; V_i at V + i * vstride.
+void launch_multidot(cudaStream_t s, const Layout& g, const double2* V, long long vstride, int m, const double2* w,
+                     double* partial, int nblk);
+void launch_multidot_final(cudaStream_t s, const double* partial, int nblk, int m, double* h, int accumulate);
+// w -= sum_i h[i] V_i; norm partials of w
+void launch_update_norm(cudaStream_t s, const Layout& g, const double2* V, long long vstride, int m, const double* h,
+                        double2* w, double* partial, int nblk);
+// x += sum_j y[j] Z_j (Z in TZ precision)
+template <typename TZ>
+void launch_lincomb(cudaStream_t s, const Layout& g, const TZ* Z, long long zstride, int m, const double* y,
+                    double2* x);
+int krylov_blocks(const Layout& g);
+
+}  // namespace svn

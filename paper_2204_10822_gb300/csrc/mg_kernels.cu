@@ -1,0 +1,554 @@
+// Stencil-form operator kernels: Jacobian apply, block-Jacobi Chebyshev
+// smoothing, bilinear restriction / prolongation, Galerkin coarse operators
+// and the dense coarsest-level solve (Section 5.4: FGMRES + multigrid with
+// three smoothing steps and a direct solve on the coarsest level).
+//
+// Templates: TS = stencil storage (double, float, __nv_bfloat16), TD = block-
+// Jacobi storage, TV = vector type (double2 / float2); arithmetic in the
+// vector's scalar type.
+#include "kernels.h"
+
+namespace svn {
+
+template <typename V> struct ScalarOf;
+template <> struct ScalarOf<double2> { using type = double; };
+template <> struct ScalarOf<float2> { using type = float; };
+
+template <typename TA, typename TS>
+__device__ __forceinline__ TA ldc(const TS* p) {
+  return (TA)to_d(*p);
+}
+template <>
+__device__ __forceinline__ float ldc<float, __nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(*p);
+}
+template <>
+__device__ __forceinline__ float ldc<float, float>(const float* p) {
+  return *p;
+}
+template <>
+__device__ __forceinline__ double ldc<double, double>(const double* p) {
+  return *p;
+}
+
+template <typename V, typename T> __device__ __forceinline__ V mk2(T a, T b);
+template <> __device__ __forceinline__ double2 mk2<double2, double>(double a, double b) { return make_double2(a, b); }
+template <> __device__ __forceinline__ float2 mk2<float2, float>(float a, float b) { return make_float2(a, b); }
+template <> __device__ __forceinline__ float2 mk2<float2, double>(double a, double b) { return make_float2((float)a, (float)b); }
+template <> __device__ __forceinline__ double2 mk2<double2, float>(float a, float b) { return make_double2(a, b); }
+
+__device__ __forceinline__ bool is_interior(int i, int j, int N) { return i >= 1 && j >= 1 && i <= N - 1 && j <= N - 1; }
+
+// y_p = sum_q K[p][q] x_q over the 9-point block stencil at node n.
+template <typename TA, typename TS, typename TX>
+__device__ __forceinline__ void stencil_row(const TS* __restrict__ st, long long pl, long long n, int ld,
+                                            const TX* __restrict__ x, TA& yx, TA& yy) {
+  const TA dxx = ldc<TA>(st + (S_D + 0) * pl + n);
+  const TA dxy = ldc<TA>(st + (S_D + 1) * pl + n);
+  const TA dyy = ldc<TA>(st + (S_D + 2) * pl + n);
+  const TX xp = x[n];
+  yx = dxx * (TA)xp.x + dxy * (TA)xp.y;
+  yy = dxy * (TA)xp.x + dyy * (TA)xp.y;
+  auto fwd = [&](int slot, long long q) {
+    const TX xq = x[q];
+    const TA b0 = ldc<TA>(st + (slot + 0) * pl + n), b1 = ldc<TA>(st + (slot + 1) * pl + n);
+    const TA b2 = ldc<TA>(st + (slot + 2) * pl + n), b3 = ldc<TA>(st + (slot + 3) * pl + n);
+    yx += b0 * (TA)xq.x + b1 * (TA)xq.y;
+    yy += b2 * (TA)xq.x + b3 * (TA)xq.y;
+  };
+  auto bwd = [&](int slot, long long q) {   // block stored at q, used transposed
+    const TX xq = x[q];
+    const TA b0 = ldc<TA>(st + (slot + 0) * pl + q), b1 = ldc<TA>(st + (slot + 1) * pl + q);
+    const TA b2 = ldc<TA>(st + (slot + 2) * pl + q), b3 = ldc<TA>(st + (slot + 3) * pl + q);
+    yx += b0 * (TA)xq.x + b2 * (TA)xq.y;
+    yy += b1 * (TA)xq.x + b3 * (TA)xq.y;
+  };
+  fwd(S_E, n + 1);
+  fwd(S_N, n + ld);
+  fwd(S_NE, n + ld + 1);
+  fwd(S_NW, n + ld - 1);
+  bwd(S_E, n - 1);
+  bwd(S_N, n - ld);
+  bwd(S_NE, n - ld - 1);
+  bwd(S_NW, n - ld + 1);
+}
+
+// Block K[p][p + (di, dj)], |di|, |dj| <= 1, as b[k][l] (row-major).
+template <typename TA, typename TS>
+__device__ __forceinline__ void get_block(const TS* __restrict__ st, long long pl, long long n, int ld, int di, int dj,
+                                          TA b[4]) {
+  if (di == 0 && dj == 0) {
+    b[0] = ldc<TA>(st + (S_D + 0) * pl + n);
+    b[1] = b[2] = ldc<TA>(st + (S_D + 1) * pl + n);
+    b[3] = ldc<TA>(st + (S_D + 2) * pl + n);
+    return;
+  }
+  int slot;
+  bool tr;
+  long long q;
+  if (dj == 0) {
+    slot = S_E; tr = di < 0; q = tr ? n - 1 : n;
+  } else if (di == 0) {
+    slot = S_N; tr = dj < 0; q = tr ? n - ld : n;
+  } else if (di == dj) {
+    slot = S_NE; tr = di < 0; q = tr ? n - ld - 1 : n;
+  } else {
+    slot = S_NW; tr = dj < 0; q = tr ? n - ld + 1 : n;
+  }
+  const TA c0 = ldc<TA>(st + (slot + 0) * pl + q), c1 = ldc<TA>(st + (slot + 1) * pl + q);
+  const TA c2 = ldc<TA>(st + (slot + 2) * pl + q), c3 = ldc<TA>(st + (slot + 3) * pl + q);
+  if (!tr) {
+    b[0] = c0; b[1] = c1; b[2] = c2; b[3] = c3;
+  } else {
+    b[0] = c0; b[1] = c2; b[2] = c1; b[3] = c3;
+  }
+}
+
+namespace {
+
+template <typename TS, typename TX, typename TY, typename TA>
+__global__ void k_apply(Layout g, const TS* __restrict__ st, const TX* __restrict__ x, TY* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > g.N || j > g.N) return;
+  const long long n = (long long)j * g.ld + i;
+  TA yx = 0, yy = 0;
+  if (is_interior(i, j, g.N)) stencil_row<TA>(st, g.plane, n, g.ld, x, yx, yy);
+  y[n] = mk2<TY>(yx, yy);
+}
+
+template <typename TS, typename TV>
+__global__ void k_residual_stencil(Layout g, const TS* __restrict__ st, const TV* __restrict__ x,
+                                   const TV* __restrict__ b, TV* __restrict__ r) {
+  using T = typename ScalarOf<TV>::type;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > g.N || j > g.N) return;
+  const long long n = (long long)j * g.ld + i;
+  T yx = 0, yy = 0;
+  TV out = mk2<TV>(T(0), T(0));
+  if (is_interior(i, j, g.N)) {
+    stencil_row<T>(st, g.plane, n, g.ld, x, yx, yy);
+    const TV bb = b[n];
+    out = mk2<TV>(bb.x - yx, bb.y - yy);
+  }
+  r[n] = out;
+}
+
+template <typename TS, typename TD>
+__global__ void k_dinv_gershgorin(Layout g, const TS* __restrict__ st, TD* __restrict__ dinv,
+                                  double* __restrict__ partial) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  double gmax = 0.0;
+  if (i <= g.N && j <= g.N) {
+    const long long n = (long long)j * g.ld + i;
+    double i00 = 0, i01 = 0, i11 = 0;
+    if (is_interior(i, j, g.N)) {
+      double d[4];
+      get_block<double>(st, g.plane, n, g.ld, 0, 0, d);
+      const double det = d[0] * d[3] - d[1] * d[1];
+      i00 = d[3] / det;
+      i01 = -d[1] / det;
+      i11 = d[0] / det;
+      double r0 = 0, r1 = 0;
+      for (int dj = -1; dj <= 1; ++dj)
+        for (int di = -1; di <= 1; ++di) {
+          if (!is_interior(i + di, j + dj, g.N)) continue;
+          double b[4];
+          get_block<double>(st, g.plane, n, g.ld, di, dj, b);
+          // rows of D^-1 B
+          r0 += fabs(i00 * b[0] + i01 * b[2]) + fabs(i00 * b[1] + i01 * b[3]);
+          r1 += fabs(i01 * b[0] + i11 * b[2]) + fabs(i01 * b[1] + i11 * b[3]);
+        }
+      gmax = fmax(r0, r1);
+    }
+    dinv[0 * g.plane + n] = (TD)i00;
+    dinv[1 * g.plane + n] = (TD)i01;
+    dinv[2 * g.plane + n] = (TD)i11;
+  }
+  gmax = block_max(gmax);
+  if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = gmax;
+}
+
+__global__ void k_max_final(const double* __restrict__ partial, int n, double* __restrict__ out) {
+  double m = 0.0;
+  for (int b = threadIdx.x; b < n; b += blockDim.x) m = fmax(m, partial[b]);
+  m = block_max(m);
+  if (threadIdx.x == 0) *out = m;
+}
+
+struct ChebCoef {
+  double theta, delta, sigma;
+};
+__device__ __forceinline__ ChebCoef cheb_coef(double lmax, double lo) {
+  ChebCoef c;
+  const double a = lo * lmax, b = lmax;
+  c.theta = 0.5 * (b + a);
+  c.delta = 0.5 * (b - a);
+  c.sigma = c.theta / c.delta;
+  return c;
+}
+
+template <typename TD, typename TV>
+__global__ void k_cheb_zero_start(Layout g, const TD* __restrict__ dinv, const double* __restrict__ lmax, double lo,
+                                  const TV* __restrict__ b, TV* __restrict__ x, TV* __restrict__ d) {
+  using T = typename ScalarOf<TV>::type;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > g.N || j > g.N) return;
+  const long long n = (long long)j * g.ld + i;
+  const ChebCoef c = cheb_coef(*lmax, lo);
+  const T it = (T)(1.0 / c.theta);
+  const TV bb = b[n];
+  const T i00 = ldc<T>(dinv + n), i01 = ldc<T>(dinv + g.plane + n), i11 = ldc<T>(dinv + 2 * g.plane + n);
+  const TV dd = mk2<TV>(it * (i00 * bb.x + i01 * bb.y), it * (i01 * bb.x + i11 * bb.y));
+  d[n] = dd;
+  x[n] = dd;
+}
+
+template <typename TS, typename TD, typename TV>
+__global__ void k_cheb_sweep(Layout g, const TS* __restrict__ st, const TD* __restrict__ dinv,
+                             const double* __restrict__ lmax, double lo, int step, const TV* __restrict__ xin,
+                             TV* __restrict__ xout, TV* __restrict__ d, const TV* __restrict__ b) {
+  using T = typename ScalarOf<TV>::type;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > g.N || j > g.N) return;
+  const long long n = (long long)j * g.ld + i;
+  if (!is_interior(i, j, g.N)) {
+    xout[n] = mk2<TV>(T(0), T(0));
+    return;
+  }
+  const ChebCoef c = cheb_coef(*lmax, lo);
+  double c1, c2;
+  if (step == 0) {
+    c1 = 0.0;
+    c2 = 1.0 / c.theta;
+  } else {
+    double rho = 1.0 / c.sigma, rn = rho;
+    for (int s = 0; s < step; ++s) {
+      rn = 1.0 / (2.0 * c.sigma - rho);
+      if (s + 1 < step) rho = rn;
+    }
+    c1 = rn * rho;
+    c2 = 2.0 * rn / c.delta;
+  }
+  T yx, yy;
+  stencil_row<T>(st, g.plane, n, g.ld, xin, yx, yy);
+  const TV bb = b[n];
+  const T rx = bb.x - yx, ry = bb.y - yy;
+  const T i00 = ldc<T>(dinv + n), i01 = ldc<T>(dinv + g.plane + n), i11 = ldc<T>(dinv + 2 * g.plane + n);
+  const TV dold = d[n];
+  const T dx = (T)c1 * dold.x + (T)c2 * (i00 * rx + i01 * ry);
+  const T dy = (T)c1 * dold.y + (T)c2 * (i01 * rx + i11 * ry);
+  d[n] = mk2<TV>(dx, dy);
+  const TV xo = xin[n];
+  xout[n] = mk2<TV>(xo.x + dx, xo.y + dy);
+}
+
+__device__ __forceinline__ double pw(int d) { return d == 0 ? 1.0 : 0.5; }
+
+template <typename TV>
+__global__ void k_restrict(Layout gf, Layout gc, const TV* __restrict__ rf, TV* __restrict__ bc) {
+  using T = typename ScalarOf<TV>::type;
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I > gc.N || J > gc.N) return;
+  const long long nc = (long long)J * gc.ld + I;
+  T sx = 0, sy = 0;
+  if (is_interior(I, J, gc.N)) {
+    for (int dj = -1; dj <= 1; ++dj)
+      for (int di = -1; di <= 1; ++di) {
+        const T w = (T)(pw(di) * pw(dj));
+        const TV r = rf[(long long)(2 * J + dj) * gf.ld + (2 * I + di)];
+        sx += w * r.x;
+        sy += w * r.y;
+      }
+  }
+  bc[nc] = mk2<TV>(sx, sy);
+}
+
+template <typename TV>
+__global__ void k_prolong_add(Layout gf, Layout gc, const TV* __restrict__ xc, TV* __restrict__ xf) {
+  using T = typename ScalarOf<TV>::type;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (!is_interior(i, j, gf.N)) return;
+  const long long n = (long long)j * gf.ld + i;
+  const int I0 = i >> 1, J0 = j >> 1;
+  const int I1 = (i & 1) ? I0 + 1 : I0, J1 = (j & 1) ? J0 + 1 : J0;
+  const T wi = (i & 1) ? T(0.5) : T(1), wj = (j & 1) ? T(0.5) : T(1);
+  T sx = 0, sy = 0;
+  // coarse boundary entries hold 0
+  const TV a = xc[(long long)J0 * gc.ld + I0];
+  sx += wi * wj * a.x; sy += wi * wj * a.y;
+  if (i & 1) {
+    const TV b = xc[(long long)J0 * gc.ld + I1];
+    sx += wi * wj * b.x; sy += wi * wj * b.y;
+  }
+  if (j & 1) {
+    const TV c = xc[(long long)J1 * gc.ld + I0];
+    sx += wi * wj * c.x; sy += wi * wj * c.y;
+  }
+  if ((i & 1) && (j & 1)) {
+    const TV d = xc[(long long)J1 * gc.ld + I1];
+    sx += wi * wj * d.x; sy += wi * wj * d.y;
+  }
+  const TV xo = xf[n];
+  xf[n] = mk2<TV>(xo.x + sx, xo.y + sy);
+}
+
+// Galerkin P^T A P, one coarse node per thread; arithmetic in double for a
+// double fine stencil, float otherwise.
+template <typename TA, typename TF, typename TC>
+__global__ void k_rap(Layout gf, Layout gc, const TF* __restrict__ stf, TC* __restrict__ stc) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (!is_interior(I, J, gc.N)) return;
+  const long long nc = (long long)J * gc.ld + I;
+  const int offs[5][2] = {{0, 0}, {1, 0}, {0, 1}, {1, 1}, {-1, 1}};
+  const int slots[5] = {S_D, S_E, S_N, S_NE, S_NW};
+#pragma unroll 1
+  for (int o = 0; o < 5; ++o) {
+    const int DI = offs[o][0], DJ = offs[o][1];
+    TA acc[4] = {0, 0, 0, 0};
+    if (is_interior(I + DI, J + DJ, gc.N)) {
+#pragma unroll 1
+      for (int dj = -1; dj <= 1; ++dj)
+#pragma unroll 1
+        for (int di = -1; di <= 1; ++di) {
+          const long long nf = (long long)(2 * J + dj) * gf.ld + (2 * I + di);
+          const TA wf = (TA)(pw(di) * pw(dj));
+          for (int ej = -1; ej <= 1; ++ej) {
+            const int oj = 2 * DJ + ej - dj;
+            if (oj < -1 || oj > 1) continue;
+            for (int ei = -1; ei <= 1; ++ei) {
+              const int oi = 2 * DI + ei - di;
+              if (oi < -1 || oi > 1) continue;
+              TA b[4];
+              get_block<TA>(stf, gf.plane, nf, gf.ld, oi, oj, b);
+              const TA w = wf * (TA)(pw(ei) * pw(ej));
+              acc[0] += w * b[0]; acc[1] += w * b[1]; acc[2] += w * b[2]; acc[3] += w * b[3];
+            }
+          }
+        }
+    }
+    if (o == 0) {
+      stc[(S_D + 0) * gc.plane + nc] = (TC)acc[0];
+      stc[(S_D + 1) * gc.plane + nc] = (TC)(0.5 * (acc[1] + acc[2]));
+      stc[(S_D + 2) * gc.plane + nc] = (TC)acc[3];
+    } else {
+      for (int e = 0; e < 4; ++e) stc[(slots[o] + e) * gc.plane + nc] = (TC)acc[e];
+    }
+  }
+}
+
+template <typename TS>
+__global__ void k_coarse_dense(Layout g, const TS* __restrict__ st, double* __restrict__ dense) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (!is_interior(i, j, g.N)) return;
+  const int m = g.N - 1, n2 = 2 * m * m;
+  const long long n = (long long)j * g.ld + i;
+  const int row = 2 * ((j - 1) * m + (i - 1));
+  for (int dj = -1; dj <= 1; ++dj)
+    for (int di = -1; di <= 1; ++di) {
+      if (!is_interior(i + di, j + dj, g.N)) continue;
+      double b[4];
+      get_block<double>(st, g.plane, n, g.ld, di, dj, b);
+      const int col = 2 * ((j + dj - 1) * m + (i + di - 1));
+      dense[(long long)row * n2 + col] = b[0];
+      dense[(long long)row * n2 + col + 1] = b[1];
+      dense[(long long)(row + 1) * n2 + col] = b[2];
+      dense[(long long)(row + 1) * n2 + col + 1] = b[3];
+    }
+}
+
+// In-place Cholesky (lower) of the n x n matrix a, then inv = a^-1 by
+// forward/back substitution of the unit columns (one column per thread).
+__global__ void k_cholesky_inverse(int n, double* __restrict__ a, double* __restrict__ inv, int* __restrict__ info) {
+  const int tid = threadIdx.x;
+  __shared__ int bad;
+  if (tid == 0) bad = 0;
+  __syncthreads();
+  for (int k = 0; k < n; ++k) {
+    if (tid == 0) {
+      const double d = a[(long long)k * n + k];
+      if (!(d > 0.0)) bad = k + 1;
+      a[(long long)k * n + k] = sqrt(fmax(d, 1e-300));
+    }
+    __syncthreads();
+    const double lkk = a[(long long)k * n + k];
+    for (int r = k + 1 + tid; r < n; r += blockDim.x) a[(long long)r * n + k] /= lkk;
+    __syncthreads();
+    const int rem = n - k - 1;
+    for (long long t = tid; t < (long long)rem * rem; t += blockDim.x) {
+      const int r = k + 1 + (int)(t / rem), c = k + 1 + (int)(t % rem);
+      if (c <= r) a[(long long)r * n + c] -= a[(long long)r * n + k] * a[(long long)c * n + k];
+    }
+    __syncthreads();
+  }
+  if (tid == 0) *info = bad;
+  for (int col = tid; col < n; col += blockDim.x) {
+    // L y = e_col
+    for (int r = 0; r < n; ++r) {
+      double s = (r == col) ? 1.0 : 0.0;
+      for (int c = 0; c < r; ++c) s -= a[(long long)r * n + c] * inv[(long long)c * n + col];
+      inv[(long long)r * n + col] = s / a[(long long)r * n + r];
+    }
+    // L^T x = y
+    for (int r = n - 1; r >= 0; --r) {
+      double s = inv[(long long)r * n + col];
+      for (int c = r + 1; c < n; ++c) s -= a[(long long)c * n + r] * inv[(long long)c * n + col];
+      inv[(long long)r * n + col] = s / a[(long long)r * n + r];
+    }
+  }
+}
+
+template <typename TV>
+__global__ void k_coarse_solve(Layout g, int n2, const double* __restrict__ inv, const TV* __restrict__ b,
+                               TV* __restrict__ x) {
+  using T = typename ScalarOf<TV>::type;
+  const int row = blockIdx.x * blockDim.x + threadIdx.x;
+  if (row >= n2) return;
+  const int m = g.N - 1;
+  double s = 0.0;
+  for (int c = 0; c < n2; c += 2) {
+    const int node = c >> 1;
+    const int ii = node % m + 1, jj = node / m + 1;
+    const TV bb = b[(long long)jj * g.ld + ii];
+    s += inv[(long long)row * n2 + c] * (double)bb.x + inv[(long long)row * n2 + c + 1] * (double)bb.y;
+  }
+  const int node = row >> 1;
+  const int ii = node % m + 1, jj = node / m + 1;
+  T* xs = reinterpret_cast<T*>(x + (long long)jj * g.ld + ii);
+  xs[row & 1] = (T)s;
+}
+
+template <typename TA, typename TB>
+__global__ void k_convert(long long n, const TA* __restrict__ a, TB* __restrict__ b) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < n) b[t] = from_d<TB>(to_d(a[t]));
+}
+
+}  // namespace
+
+// ---- launchers -----------------------------------------------------------------------
+static const dim3 kBlk(32, 8);
+static inline dim3 ngrid(const Layout& g) { return dim3((g.n1 + kBlk.x - 1) / kBlk.x, (g.n1 + kBlk.y - 1) / kBlk.y); }
+
+template <typename TS, typename TX, typename TY, typename TA>
+void launch_apply(cudaStream_t s, const Layout& g, const TS* st, const TX* x, TY* y) {
+  k_apply<TS, TX, TY, TA><<<ngrid(g), kBlk, 0, s>>>(g, st, x, y);
+}
+template void launch_apply<double, double2, double2, double>(cudaStream_t, const Layout&, const double*,
+                                                             const double2*, double2*);
+template void launch_apply<double, float2, double2, double>(cudaStream_t, const Layout&, const double*,
+                                                            const float2*, double2*);
+template void launch_apply<float, float2, float2, float>(cudaStream_t, const Layout&, const float*, const float2*,
+                                                         float2*);
+template void launch_apply<__nv_bfloat16, float2, float2, float>(cudaStream_t, const Layout&, const __nv_bfloat16*,
+                                                                 const float2*, float2*);
+
+template <typename TS, typename TV>
+void launch_residual_stencil(cudaStream_t s, const Layout& g, const TS* st, const TV* x, const TV* b, TV* r) {
+  k_residual_stencil<TS, TV><<<ngrid(g), kBlk, 0, s>>>(g, st, x, b, r);
+}
+
+template <typename TS, typename TD>
+int launch_dinv_gershgorin(cudaStream_t s, const Layout& g, const TS* st, TD* dinv, double* partial) {
+  dim3 gr = ngrid(g);
+  k_dinv_gershgorin<TS, TD><<<gr, kBlk, 0, s>>>(g, st, dinv, partial);
+  return gr.x * gr.y;
+}
+
+void launch_max_final(cudaStream_t s, const double* partial, int n, double* out) {
+  k_max_final<<<1, 1024, 0, s>>>(partial, n, out);
+}
+
+template <typename TS, typename TD, typename TV>
+void launch_cheb_zero_start(cudaStream_t s, const Layout& g, const TD* dinv, const double* lmax, double lo,
+                            const TV* b, TV* x, TV* d) {
+  k_cheb_zero_start<TD, TV><<<ngrid(g), kBlk, 0, s>>>(g, dinv, lmax, lo, b, x, d);
+}
+
+template <typename TS, typename TD, typename TV>
+void launch_cheb_sweep(cudaStream_t s, const Layout& g, const TS* st, const TD* dinv, const double* lmax, double lo,
+                       int step, const TV* xin, TV* xout, TV* d, const TV* b) {
+  k_cheb_sweep<TS, TD, TV><<<ngrid(g), kBlk, 0, s>>>(g, st, dinv, lmax, lo, step, xin, xout, d, b);
+}
+
+template <typename TV>
+void launch_restrict(cudaStream_t s, const Layout& gf, const Layout& gc, const TV* rf, TV* bc) {
+  k_restrict<TV><<<ngrid(gc), kBlk, 0, s>>>(gf, gc, rf, bc);
+}
+
+template <typename TV>
+void launch_prolong_add(cudaStream_t s, const Layout& gf, const Layout& gc, const TV* xc, TV* xf) {
+  k_prolong_add<TV><<<ngrid(gf), kBlk, 0, s>>>(gf, gc, xc, xf);
+}
+
+template <typename TF, typename TC>
+void launch_rap(cudaStream_t s, const Layout& gf, const Layout& gc, const TF* stf, TC* stc) {
+  using TA = typename std::conditional<std::is_same<TF, double>::value, double, float>::type;
+  k_rap<TA, TF, TC><<<ngrid(gc), kBlk, 0, s>>>(gf, gc, stf, stc);
+}
+
+template <typename TS>
+void launch_coarse_dense(cudaStream_t s, const Layout& g, const TS* st, double* dense) {
+  const int m = g.N - 1, n2 = 2 * m * m;
+  cudaMemsetAsync(dense, 0, sizeof(double) * (size_t)n2 * n2, s);
+  k_coarse_dense<TS><<<ngrid(g), kBlk, 0, s>>>(g, st, dense);
+}
+
+void launch_cholesky_inverse(cudaStream_t s, int n, double* a, double* inv, int* info) {
+  k_cholesky_inverse<<<1, 256, 0, s>>>(n, a, inv, info);
+}
+
+template <typename TV>
+void launch_coarse_solve(cudaStream_t s, const Layout& g, int n2, const double* inv, const TV* b, TV* x) {
+  cudaMemsetAsync(x, 0, sizeof(TV) * g.plane, s);
+  k_coarse_solve<TV><<<(n2 + 127) / 128, 128, 0, s>>>(g, n2, inv, b, x);
+}
+
+template <typename TA, typename TB>
+void launch_convert_stencil(cudaStream_t s, const Layout& g, const TA* a, TB* b) {
+  const long long n = (long long)NSTEN * g.plane;
+  k_convert<TA, TB><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, a, b);
+}
+
+// explicit instantiations: FP64 path (double stencil, double vectors) and
+// mixed path (bf16 / float stencils, float vectors)
+#define SVN_INST_LEVEL(TS, TD, TV)                                                                                 \
+  template void launch_residual_stencil<TS, TV>(cudaStream_t, const Layout&, const TS*, const TV*, const TV*,    \
+                                                TV*);                                                            \
+  template int launch_dinv_gershgorin<TS, TD>(cudaStream_t, const Layout&, const TS*, TD*, double*);             \
+  template void launch_cheb_zero_start<TS, TD, TV>(cudaStream_t, const Layout&, const TD*, const double*, double, \
+                                                   const TV*, TV*, TV*);                                         \
+  template void launch_cheb_sweep<TS, TD, TV>(cudaStream_t, const Layout&, const TS*, const TD*, const double*,   \
+                                              double, int, const TV*, TV*, TV*, const TV*);                      \
+  template void launch_coarse_dense<TS>(cudaStream_t, const Layout&, const TS*, double*);
+
+SVN_INST_LEVEL(double, double, double2)
+SVN_INST_LEVEL(__nv_bfloat16, float, float2)
+SVN_INST_LEVEL(float, float, float2)
+
+template int launch_dinv_gershgorin<double, float>(cudaStream_t, const Layout&, const double*, float*, double*);
+template void launch_restrict<double2>(cudaStream_t, const Layout&, const Layout&, const double2*, double2*);
+template void launch_restrict<float2>(cudaStream_t, const Layout&, const Layout&, const float2*, float2*);
+template void launch_prolong_add<double2>(cudaStream_t, const Layout&, const Layout&, const double2*, double2*);
+template void launch_prolong_add<float2>(cudaStream_t, const Layout&, const Layout&, const float2*, float2*);
+template void launch_coarse_solve<double2>(cudaStream_t, const Layout&, int, const double*, const double2*,
+                                           double2*);
+template void launch_coarse_solve<float2>(cudaStream_t, const Layout&, int, const double*, const float2*, float2*);
+template void launch_rap<double, double>(cudaStream_t, const Layout&, const Layout&, const double*, double*);
+template void launch_rap<float, float>(cudaStream_t, const Layout&, const Layout&, const float*, float*);
+template void launch_rap<double, float>(cudaStream_t, const Layout&, const Layout&, const double*, float*);
+template void launch_convert_stencil<double, __nv_bfloat16>(cudaStream_t, const Layout&, const double*,
+                                                            __nv_bfloat16*);
+template void launch_convert_stencil<double, float>(cudaStream_t, const Layout&, const double*, float*);
+template void launch_convert_stencil<float, __nv_bfloat16>(cudaStream_t, const Layout&, const float*,
+                                                           __nv_bfloat16*);
+
+}  // namespace svn

@@ -1,0 +1,830 @@
+// Host orchestration of the svN implicit step and the C ABI of include/svn.h.
+//
+// Per Newton iteration (Sections 4.2, 5.1, 5.4):
+//   residual R(v_l) and ||R||            -> stop test
+//   linearisation at (v_l, pi_l)         -> level-0 stencil, Galerkin hierarchy
+//   FGMRES(K dv = -R), V-cycle preconditioner
+//   backtracking on Phi                  -> alpha
+//   pi <- pi + alpha pi~,  v <- v + alpha dv
+// All arithmetic runs in the CUDA kernels; the host only reads the handful of
+// scalars that steer the iteration (norms, energies, the Hessenberg column).
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/svn.h"
+#include "kernels.h"
+
+using namespace svn;
+
+namespace {
+
+struct Level {
+  Layout g;
+  double* st64 = nullptr;        // FP64 stencil (19 planes)
+  __nv_bfloat16* st16 = nullptr; // mixed: BF16 copy used by the V-cycle
+  void* dinv = nullptr;          // 3 planes (double or float)
+  double* lmax = nullptr;        // device scalar: Gershgorin bound of D^-1 A
+  void* x[2] = {nullptr, nullptr};
+  void* d = nullptr;
+  void* b = nullptr;
+  void* r = nullptr;
+};
+
+}  // namespace
+
+struct svn_handle {
+  svn_grid grid{};
+  svn_params prm{};
+  cudaStream_t stream = nullptr;
+  std::string err;
+  int device = 0;
+  bool mixed = false;
+
+  Layout g0{};
+  std::vector<Level> lv;
+  int ncoarse = 0;              // dense size of the coarsest level
+  double* dense = nullptr;      // coarsest matrix (factored in place)
+  double* dense_inv = nullptr;  // its inverse
+  int* info = nullptr;
+
+  // forcing (caller layout) and precomputed fields
+  double *in_h = nullptr, *in_A = nullptr, *in_wind = nullptr, *in_ocean = nullptr, *in_vold = nullptr;
+  bool have_forcing = false;
+  double *P = nullptr, *rhoH = nullptr, *fq = nullptr, *voq = nullptr;
+  double cur_dt = -1.0;
+
+  // Newton state
+  double2 *v = nullptr, *dv = nullptr, *vt = nullptr, *R = nullptr, *rhs = nullptr;
+  double* pi = nullptr;
+  double* pi_scratch = nullptr;
+  bool state_set = false;
+  double* eb = nullptr;         // element buffer, NELEM planes FP64
+
+  // Krylov
+  int restart = 30;
+  double2* V = nullptr;
+  void* Z = nullptr;            // restart vectors in the V-cycle precision
+  double2* w = nullptr;
+  double* hbuf = nullptr;       // device: h1 [restart+1], h2 [restart+1], nrm2
+  double* ybuf = nullptr;       // device: FGMRES coefficients
+  double* partial = nullptr;    // reduction partials
+  size_t partial_len = 0;
+  double* scal = nullptr;       // device scalars
+  double* hostbuf = nullptr;    // pinned host mirror
+  size_t hostbuf_len = 0;
+};
+
+namespace {
+
+int fail(svn_handle* h, int code, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (h) h->err = buf;
+  return code;
+}
+
+#define CK(call)                                                                                        \
+  do {                                                                                                  \
+    cudaError_t e_ = (call);                                                                            \
+    if (e_ != cudaSuccess) return fail(h, SVN_ERR_CUDA, "%s failed: %s", #call, cudaGetErrorString(e_)); \
+  } while (0)
+
+#define CKL()                                                                                      \
+  do {                                                                                             \
+    cudaError_t e_ = cudaGetLastError();                                                           \
+    if (e_ != cudaSuccess) return fail(h, SVN_ERR_CUDA, "kernel launch: %s", cudaGetErrorString(e_)); \
+  } while (0)
+
+#define TRY(expr)            \
+  do {                       \
+    int rc_ = (expr);        \
+    if (rc_ != SVN_OK) return rc_; \
+  } while (0)
+
+template <typename T>
+int dalloc(svn_handle* h, T** p, size_t n) {
+  cudaError_t e = cudaMalloc((void**)p, sizeof(T) * (n ? n : 1));
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(h, SVN_ERR_OOM, "cudaMalloc of %zu bytes failed: %s", sizeof(T) * n, cudaGetErrorString(e));
+  }
+  e = cudaMemset(*p, 0, sizeof(T) * (n ? n : 1));
+  if (e != cudaSuccess) return fail(h, SVN_ERR_CUDA, "cudaMemset: %s", cudaGetErrorString(e));
+  return SVN_OK;
+}
+
+template <typename T>
+void dfree(T*& p) {
+  if (p) cudaFree((void*)p);
+  p = nullptr;
+}
+
+Phys make_phys(const svn_handle* h, const Layout& g, double dt) {
+  Phys ph;
+  const double e = h->prm.e;
+  ph.dt = dt;
+  ph.dx = g.dx;
+  ph.w = 0.25 * g.dx * g.dx;
+  ph.ta = 0.5 * (1.0 + 1.0 / e);
+  ph.tb = 0.5 * (1.0 - 1.0 / e);
+  ph.tc = 0.5 / e;
+  ph.dmin2 = h->prm.delta_min * h->prm.delta_min;
+  ph.cdrag = h->prm.Co * h->prm.rho_o;
+  return ph;
+}
+
+PhysConst make_pc(const svn_params& p) {
+  PhysConst c;
+  c.rho_ice = p.rho_ice; c.rho_a = p.rho_a; c.rho_o = p.rho_o; c.Ca = p.Ca; c.Co = p.Co;
+  c.f_c = p.f_c; c.Pstar = p.Pstar; c.C = p.C; c.e = p.e; c.delta_min = p.delta_min;
+  return c;
+}
+
+int sync_read(svn_handle* h, const double* dsrc, size_t n, double* out) {
+  CK(cudaMemcpyAsync(h->hostbuf, dsrc, sizeof(double) * n, cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  memcpy(out, h->hostbuf, sizeof(double) * n);
+  return SVN_OK;
+}
+
+// ---- step pieces ------------------------------------------------------------------
+int precompute(svn_handle* h, double dt) {
+  if (!h->have_forcing) return fail(h, SVN_ERR_STATE, "svn_set_forcing has not been called");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(h, SVN_ERR_ARG, "dt must be positive and finite");
+  launch_precompute(h->stream, h->g0, dt, make_pc(h->prm), h->in_h, h->in_A, h->in_wind, h->in_ocean, h->in_vold,
+                    h->P, h->rhoH, h->fq, h->voq);
+  CKL();
+  h->cur_dt = dt;
+  return SVN_OK;
+}
+
+int residual(svn_handle* h, const double2* v, double2* R, double* norm) {
+  const Phys ph = make_phys(h, h->g0, h->cur_dt);
+  launch_residual(h->stream, h->g0, ph, v, h->P, h->rhoH, h->fq, h->voq, h->eb, R, h->partial);
+  launch_sum_final(h->stream, h->partial, residual_partials(h->g0), h->scal);
+  CKL();
+  double s;
+  TRY(sync_read(h, h->scal, 1, &s));
+  *norm = std::sqrt(s);
+  return SVN_OK;
+}
+
+int energy(svn_handle* h, const double2* v, const double2* dv, const double* alphas, int k, double* phi,
+           double* scale) {
+  if (k < 1 || k > MAX_ALPHA) return fail(h, SVN_ERR_ARG, "energy: 1 <= k <= %d", MAX_ALPHA);
+  const Phys ph = make_phys(h, h->g0, h->cur_dt);
+  AlphaSet al{};
+  for (int a = 0; a < k; ++a) al.a[a] = alphas[a];
+  launch_energy(h->stream, h->g0, ph, k, al, v, dv, h->P, h->rhoH, h->fq, h->voq, h->partial, h->scal);
+  CKL();
+  double out[MAX_ALPHA + 1];
+  TRY(sync_read(h, h->scal, MAX_ALPHA + 1, out));
+  for (int a = 0; a < k; ++a) phi[a] = out[a];
+  if (scale) *scale = out[MAX_ALPHA];
+  return SVN_OK;
+}
+
+int linearize(svn_handle* h, const double2* v, const double* pi) {
+  const Phys ph = make_phys(h, h->g0, h->cur_dt);
+  cudaStream_t s = h->stream;
+  launch_element_matrices<double>(s, h->g0, ph, v, pi, h->P, h->rhoH, h->voq, h->eb, nullptr);
+  launch_stencil_from_elements<double, double>(s, h->g0, h->eb, h->lv[0].st64);
+  CKL();
+  const int L = (int)h->lv.size();
+  for (int l = 1; l < L; ++l) launch_rap<double, double>(s, h->lv[l - 1].g, h->lv[l].g, h->lv[l - 1].st64, h->lv[l].st64);
+  CKL();
+  for (int l = 0; l < L - 1; ++l) {
+    Level& lv = h->lv[l];
+    int nb;
+    if (h->mixed) {
+      launch_convert_stencil<double, __nv_bfloat16>(s, lv.g, lv.st64, lv.st16);
+      nb = launch_dinv_gershgorin<double, float>(s, lv.g, lv.st64, (float*)lv.dinv, h->partial);
+    } else {
+      nb = launch_dinv_gershgorin<double, double>(s, lv.g, lv.st64, (double*)lv.dinv, h->partial);
+    }
+    launch_max_final(s, h->partial, nb, lv.lmax);
+  }
+  CKL();
+  Level& lc = h->lv[L - 1];
+  launch_coarse_dense<double>(s, lc.g, lc.st64, h->dense);
+  launch_cholesky_inverse(s, h->ncoarse, h->dense, h->dense_inv, h->info);
+  CKL();
+  int info = 0;
+  CK(cudaMemcpyAsync(h->hostbuf, h->info, sizeof(int), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  memcpy(&info, h->hostbuf, sizeof(int));
+  if (info != 0) return fail(h, SVN_ERR_ARG, "coarsest operator is not positive definite (pivot %d)", info);
+  return SVN_OK;
+}
+
+// One V-cycle on levels l..L-1: x_l = M_l^-1 b_l, both in level-l vectors (TV).
+template <typename TS, typename TD, typename TV>
+void vcycle(svn_handle* h, int l, const TV* b, TV* xout) {
+  cudaStream_t s = h->stream;
+  const int L = (int)h->lv.size();
+  Level& lv = h->lv[l];
+  if (l == L - 1) {
+    launch_coarse_solve<TV>(s, lv.g, h->ncoarse, h->dense_inv, b, xout);
+    return;
+  }
+  const TS* st = h->mixed ? (const TS*)lv.st16 : (const TS*)lv.st64;
+  const TD* dinv = (const TD*)lv.dinv;
+  TV* x0 = (TV*)lv.x[0];
+  TV* x1 = (TV*)lv.x[1];
+  TV* d = (TV*)lv.d;
+  TV* r = (TV*)lv.r;
+  const int deg = h->prm.cheb_degree;
+  const double lo = h->prm.cheb_lo;
+  // pre-smoothing from x = 0
+  launch_cheb_zero_start<TS, TD, TV>(s, lv.g, dinv, lv.lmax, lo, b, x0, d);
+  TV* cur = x0;
+  TV* nxt = x1;
+  for (int k = 1; k < deg; ++k) {
+    launch_cheb_sweep<TS, TD, TV>(s, lv.g, st, dinv, lv.lmax, lo, k, cur, nxt, d, b);
+    std::swap(cur, nxt);
+  }
+  // coarse-grid correction
+  launch_residual_stencil<TS, TV>(s, lv.g, st, cur, b, r);
+  Level& lc = h->lv[l + 1];
+  launch_restrict<TV>(s, lv.g, lc.g, r, (TV*)lc.b);
+  vcycle<TS, TD, TV>(h, l + 1, (const TV*)lc.b, (TV*)lc.x[0]);
+  launch_prolong_add<TV>(s, lv.g, lc.g, (const TV*)lc.x[0], cur);
+  // post-smoothing (same polynomial), the last sweep writing xout when it can
+  for (int k = 0; k < deg; ++k) {
+    TV* dst = (k == deg - 1 && xout != cur) ? xout : (cur == x0 ? x1 : x0);
+    launch_cheb_sweep<TS, TD, TV>(s, lv.g, st, dinv, lv.lmax, lo, k, cur, dst, d, b);
+    cur = dst;
+  }
+  if (cur != xout) cudaMemcpyAsync(xout, cur, sizeof(TV) * lv.g.plane, cudaMemcpyDeviceToDevice, s);
+  (void)nxt;
+}
+
+// z = M^-1 r for a level-0 FP64 vector r; z in the V-cycle precision.
+int precondition(svn_handle* h, const double2* r, void* z) {
+  Level& l0 = h->lv[0];
+  if (h->mixed) {
+    launch_cast_d2f(h->stream, l0.g, r, (float2*)l0.b);
+    vcycle<__nv_bfloat16, float, float2>(h, 0, (const float2*)l0.b, (float2*)z);
+  } else {
+    vcycle<double, double, double2>(h, 0, r, (double2*)z);
+  }
+  CKL();
+  return SVN_OK;
+}
+
+// y = K0 z (FP64 outer operator), z in the V-cycle precision.
+void apply_outer(svn_handle* h, const void* z, double2* y) {
+  if (h->mixed)
+    launch_apply<double, float2, double2, double>(h->stream, h->g0, h->lv[0].st64, (const float2*)z, y);
+  else
+    launch_apply<double, double2, double2, double>(h->stream, h->g0, h->lv[0].st64, (const double2*)z, y);
+}
+
+size_t zbytes(const svn_handle* h) { return (h->mixed ? sizeof(float2) : sizeof(double2)) * h->g0.plane; }
+void* zvec(svn_handle* h, int j) { return (char*)h->Z + (size_t)j * zbytes(h); }
+
+int norm2(svn_handle* h, const double2* x, double* out) {
+  launch_norm2_partial(h->stream, h->g0, x, h->partial);
+  launch_sum_final(h->stream, h->partial, reduce_blocks(h->g0.plane), h->scal);
+  CKL();
+  double s;
+  TRY(sync_read(h, h->scal, 1, &s));
+  *out = std::sqrt(s);
+  return SVN_OK;
+}
+
+// FGMRES (right preconditioned, CGS2 Arnoldi) for K x = b, x = 0 on entry.
+int fgmres(svn_handle* h, const double2* b, double2* x, double rtol, int maxit, int* iters) {
+  cudaStream_t s = h->stream;
+  const Layout& g = h->g0;
+  const int m = h->restart;
+  const long long vs = g.plane;
+  const int nw = krylov_blocks(g);
+  CK(cudaMemsetAsync(x, 0, sizeof(double2) * g.plane, s));
+  double bnorm;
+  TRY(norm2(h, b, &bnorm));
+  *iters = 0;
+  if (bnorm == 0.0) return SVN_OK;
+  if (!std::isfinite(bnorm)) return fail(h, SVN_ERR_NONFINITE, "FGMRES: non-finite right-hand side");
+  std::vector<double> H((size_t)(m + 1) * m), cs(m), sn(m), gv(m + 1), yv(m);
+  double beta = bnorm;
+  launch_scale_to(s, g, 1.0 / beta, b, h->V);   // V0 = b / beta
+  int total = 0;
+  bool done = false;
+  while (!done) {
+    std::fill(H.begin(), H.end(), 0.0);
+    std::fill(gv.begin(), gv.end(), 0.0);
+    gv[0] = beta;
+    int jdone = 0;
+    for (int j = 0; j < m; ++j) {
+      double2* Vj = h->V + (size_t)j * vs;
+      TRY(precondition(h, Vj, zvec(h, j)));
+      apply_outer(h, zvec(h, j), h->w);
+      // classical Gram-Schmidt, twice
+      double* h1 = h->hbuf;
+      double* h2 = h->hbuf + (m + 1);
+      double* nr = h->hbuf + 2 * (m + 1);
+      launch_multidot(s, g, h->V, vs, j + 1, h->w, h->partial, nw);
+      launch_multidot_final(s, h->partial, nw, j + 1, h1, 0);
+      launch_update_norm(s, g, h->V, vs, j + 1, h1, h->w, h->partial, nw);
+      launch_multidot(s, g, h->V, vs, j + 1, h->w, h->partial, nw);
+      launch_multidot_final(s, h->partial, nw, j + 1, h2, 0);
+      launch_update_norm(s, g, h->V, vs, j + 1, h2, h->w, h->partial, nw);
+      launch_sum_final(s, h->partial, nw, nr);
+      CKL();
+      std::vector<double> hh(2 * (m + 1) + 1);
+      TRY(sync_read(h, h->hbuf, hh.size(), hh.data()));
+      for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hh[i] + hh[m + 1 + i];
+      const double hn = std::sqrt(hh[2 * (m + 1)]);
+      if (!std::isfinite(hn)) return fail(h, SVN_ERR_NONFINITE, "FGMRES: non-finite Arnoldi vector");
+      H[(size_t)(j + 1) * m + j] = hn;
+      if (hn > 0.0) {
+        launch_scale_to(s, g, 1.0 / hn, h->w, h->V + (size_t)(j + 1) * vs);   // V_{j+1} = w / hn
+        CKL();
+      }
+      for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * H[(size_t)i * m + j] + sn[i] * H[(size_t)(i + 1) * m + j];
+        H[(size_t)(i + 1) * m + j] = -sn[i] * H[(size_t)i * m + j] + cs[i] * H[(size_t)(i + 1) * m + j];
+        H[(size_t)i * m + j] = t;
+      }
+      const double a = H[(size_t)j * m + j], bb = H[(size_t)(j + 1) * m + j];
+      const double den = std::hypot(a, bb);
+      if (den == 0.0) return fail(h, SVN_ERR_KRYLOV, "FGMRES breakdown (zero Hessenberg column)");
+      cs[j] = a / den;
+      sn[j] = bb / den;
+      H[(size_t)j * m + j] = den;
+      H[(size_t)(j + 1) * m + j] = 0.0;
+      gv[j + 1] = -sn[j] * gv[j];
+      gv[j] = cs[j] * gv[j];
+      ++total;
+      jdone = j + 1;
+      if (std::fabs(gv[j + 1]) <= rtol * bnorm || total >= maxit || hn == 0.0) break;
+    }
+    // y = H^-1 g (upper triangular), x += Z y
+    for (int i = jdone - 1; i >= 0; --i) {
+      double sacc = gv[i];
+      for (int k = i + 1; k < jdone; ++k) sacc -= H[(size_t)i * m + k] * yv[k];
+      yv[i] = sacc / H[(size_t)i * m + i];
+    }
+    memcpy(h->hostbuf, yv.data(), sizeof(double) * jdone);
+    CK(cudaMemcpyAsync(h->ybuf, h->hostbuf, sizeof(double) * jdone, cudaMemcpyHostToDevice, s));
+    if (h->mixed)
+      launch_lincomb<float2>(s, g, (const float2*)h->Z, vs, jdone, h->ybuf, x);
+    else
+      launch_lincomb<double2>(s, g, (const double2*)h->Z, vs, jdone, h->ybuf, x);
+    CKL();
+    CK(cudaStreamSynchronize(s));   // hostbuf reuse
+    const double est = std::fabs(gv[jdone]);
+    if (est <= rtol * bnorm) break;
+    if (total >= maxit) break;   // inexact Newton direction; the line search safeguards it
+    // restart: V0 = (b - K x) / |b - K x|
+    launch_apply<double, double2, double2, double>(s, g, h->lv[0].st64, x, h->w);
+    launch_axpby_to(s, g, b, -1.0, h->w, h->w);
+    CKL();
+    TRY(norm2(h, h->w, &beta));
+    if (beta <= rtol * bnorm) break;
+    launch_scale_to(s, g, 1.0 / beta, h->w, h->V);
+    CKL();
+  }
+  *iters = total;
+  return SVN_OK;
+}
+
+int check_params(svn_handle* h, const svn_params* p) {
+  if (!(p->e > 0) || !(p->delta_min > 0) || !(p->rho_ice > 0) || p->Pstar < 0 || p->Co < 0 || p->Ca < 0)
+    return fail(h, SVN_ERR_ARG, "invalid physical constants");
+  if (p->max_newton < 0 || p->max_newton > SVN_MAX_NEWTON) return fail(h, SVN_ERR_ARG, "max_newton out of range");
+  if (p->max_halvings < 0 || p->max_halvings > 60) return fail(h, SVN_ERR_ARG, "max_halvings out of range");
+  if (p->restart < 1 || p->restart > 200) return fail(h, SVN_ERR_ARG, "restart must be in [1, 200]");
+  if (p->cheb_degree < 1 || p->cheb_degree > 16) return fail(h, SVN_ERR_ARG, "cheb_degree must be in [1, 16]");
+  if (!(p->cheb_lo > 0.0 && p->cheb_lo < 1.0)) return fail(h, SVN_ERR_ARG, "cheb_lo must be in (0, 1)");
+  if (p->precision != SVN_FP64 && p->precision != SVN_MIXED) return fail(h, SVN_ERR_ARG, "unknown precision");
+  if (p->coarse_N < 2 || p->coarse_N > 16) return fail(h, SVN_ERR_ARG, "coarse_N must be in [2, 16]");
+  return SVN_OK;
+}
+
+int create_impl(svn_handle* h, const svn_grid* g, const svn_params* p, void* stream) {
+  if (!g || !p) return fail(h, SVN_ERR_ARG, "NULL grid or params");
+  if (g->N < 8 || g->N > 16384 || (g->N & 1)) return fail(h, SVN_ERR_ARG, "N must be even and in [8, 16384]");
+  if (!(g->L > 0) || !std::isfinite(g->L)) return fail(h, SVN_ERR_ARG, "L must be positive");
+  TRY(check_params(h, p));
+  h->grid = *g;
+  h->prm = *p;
+  h->stream = (cudaStream_t)stream;
+  h->mixed = p->precision == SVN_MIXED;
+  h->restart = p->restart;
+  CK(cudaGetDevice(&h->device));
+  h->g0 = make_layout(g->N, g->L);
+  // multigrid levels: halve while even and above coarse_N
+  int n = g->N;
+  h->lv.clear();
+  while (true) {
+    Level L;
+    L.g = make_layout(n, g->L);
+    h->lv.push_back(L);
+    if (n <= p->coarse_N || (n & 1) || n / 2 < 2) break;
+    n /= 2;
+  }
+  const Layout& g0 = h->g0;
+  const long long pl = g0.plane;
+  TRY(dalloc(h, &h->in_h, (size_t)g->N * g->N));
+  TRY(dalloc(h, &h->in_A, (size_t)g->N * g->N));
+  const size_t nv = 2 * (size_t)(g->N + 1) * (g->N + 1);
+  TRY(dalloc(h, &h->in_wind, nv));
+  TRY(dalloc(h, &h->in_ocean, nv));
+  TRY(dalloc(h, &h->in_vold, nv));
+  TRY(dalloc(h, &h->P, pl));
+  TRY(dalloc(h, &h->rhoH, pl));
+  TRY(dalloc(h, &h->fq, 8 * pl));
+  TRY(dalloc(h, &h->voq, 8 * pl));
+  TRY(dalloc(h, &h->v, pl));
+  TRY(dalloc(h, &h->dv, pl));
+  TRY(dalloc(h, &h->vt, pl));
+  TRY(dalloc(h, &h->R, pl));
+  TRY(dalloc(h, &h->rhs, pl));
+  TRY(dalloc(h, &h->w, pl));
+  TRY(dalloc(h, &h->pi, 12 * pl));
+  TRY(dalloc(h, &h->eb, (size_t)NELEM * pl));
+  const size_t vsz = h->mixed ? sizeof(float2) : sizeof(double2);
+  for (size_t l = 0; l < h->lv.size(); ++l) {
+    Level& L = h->lv[l];
+    const long long lp = L.g.plane;
+    TRY(dalloc(h, &L.st64, (size_t)NSTEN * lp));
+    if (h->mixed) TRY(dalloc(h, &L.st16, (size_t)NSTEN * lp));
+    TRY(dalloc(h, (char**)&L.dinv, 3 * lp * (h->mixed ? sizeof(float) : sizeof(double))));
+    TRY(dalloc(h, &L.lmax, 1));
+    for (int k = 0; k < 2; ++k) TRY(dalloc(h, (char**)&L.x[k], lp * vsz));
+    TRY(dalloc(h, (char**)&L.d, lp * vsz));
+    TRY(dalloc(h, (char**)&L.b, lp * vsz));
+    TRY(dalloc(h, (char**)&L.r, lp * vsz));
+  }
+  const int mc = h->lv.back().g.N - 1;
+  h->ncoarse = 2 * mc * mc;
+  TRY(dalloc(h, &h->dense, (size_t)h->ncoarse * h->ncoarse));
+  TRY(dalloc(h, &h->dense_inv, (size_t)h->ncoarse * h->ncoarse));
+  TRY(dalloc(h, &h->info, 4));
+  TRY(dalloc(h, &h->V, (size_t)(h->restart + 1) * pl));
+  TRY(dalloc(h, (char**)&h->Z, (size_t)h->restart * pl * vsz));
+  TRY(dalloc(h, &h->hbuf, 2 * (size_t)(h->restart + 1) + 1));
+  TRY(dalloc(h, &h->ybuf, (size_t)h->restart + 1));
+  const int nw = krylov_blocks(g0);
+  h->partial_len = (size_t)std::max<long long>(
+      {(long long)nw * (h->restart + 1), (long long)residual_partials(g0), (long long)energy_partials(g0) * (2 * MAX_ALPHA + 1),
+       (long long)reduce_blocks(pl), 4096});
+  TRY(dalloc(h, &h->partial, h->partial_len));
+  TRY(dalloc(h, &h->scal, 64));
+  h->hostbuf_len = 4 * (size_t)(h->restart + 2) + 64;
+  CK(cudaMallocHost((void**)&h->hostbuf, sizeof(double) * h->hostbuf_len));
+  return SVN_OK;
+}
+
+void destroy_impl(svn_handle* h) {
+  dfree(h->in_h); dfree(h->in_A); dfree(h->in_wind); dfree(h->in_ocean); dfree(h->in_vold);
+  dfree(h->P); dfree(h->rhoH); dfree(h->fq); dfree(h->voq);
+  dfree(h->v); dfree(h->dv); dfree(h->vt); dfree(h->R); dfree(h->rhs); dfree(h->w);
+  dfree(h->pi); dfree(h->pi_scratch); dfree(h->eb);
+  for (Level& L : h->lv) {
+    dfree(L.st64); dfree(L.st16); dfree(L.dinv); dfree(L.lmax);
+    dfree(L.x[0]); dfree(L.x[1]); dfree(L.d); dfree(L.b); dfree(L.r);
+  }
+  dfree(h->dense); dfree(h->dense_inv); dfree(h->info);
+  dfree(h->V); dfree(h->Z); dfree(h->hbuf); dfree(h->ybuf); dfree(h->partial); dfree(h->scal);
+  if (h->hostbuf) cudaFreeHost(h->hostbuf);
+  h->hostbuf = nullptr;
+}
+
+// Validate the device copies of the inputs (counts of bad entries, one read-back).
+int validate_forcing(svn_handle* h) {
+  const long long nc = (long long)h->grid.N * h->grid.N;
+  const long long nv = 2LL * (h->grid.N + 1) * (h->grid.N + 1);
+  int* flags = (int*)h->info;   // 4 ints: info + 3 counters
+  CK(cudaMemsetAsync(flags + 1, 0, 3 * sizeof(int), h->stream));
+  launch_validate(h->stream, nc, nv, h->in_h, h->in_A, h->in_wind, h->in_ocean, h->in_vold, flags + 1);
+  CKL();
+  int cnt[3];
+  CK(cudaMemcpyAsync(h->hostbuf, flags + 1, sizeof(cnt), cudaMemcpyDeviceToHost, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  memcpy(cnt, h->hostbuf, sizeof(cnt));
+  if (cnt[0]) return fail(h, SVN_ERR_NONFINITE, "%d non-finite input entries", cnt[0]);
+  if (cnt[1]) return fail(h, SVN_ERR_ARG, "%d cells with thickness <= 0", cnt[1]);
+  if (cnt[2]) return fail(h, SVN_ERR_ARG, "%d cells with concentration outside [0, 1]", cnt[2]);
+  return SVN_OK;
+}
+
+int set_forcing_impl(svn_handle* h, const double* hc, const double* A, const double* wind, const double* ocean,
+                     const double* vold, bool host) {
+  if (!hc || !A || !wind || !ocean || !vold) return fail(h, SVN_ERR_ARG, "NULL forcing pointer");
+  const size_t nc = (size_t)h->grid.N * h->grid.N;
+  const size_t nv = 2 * (size_t)(h->grid.N + 1) * (h->grid.N + 1);
+  const cudaMemcpyKind kind = host ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToDevice;
+  CK(cudaMemcpyAsync(h->in_h, hc, sizeof(double) * nc, kind, h->stream));
+  CK(cudaMemcpyAsync(h->in_A, A, sizeof(double) * nc, kind, h->stream));
+  CK(cudaMemcpyAsync(h->in_wind, wind, sizeof(double) * nv, kind, h->stream));
+  CK(cudaMemcpyAsync(h->in_ocean, ocean, sizeof(double) * nv, kind, h->stream));
+  CK(cudaMemcpyAsync(h->in_vold, vold, sizeof(double) * nv, kind, h->stream));
+  h->have_forcing = false;
+  TRY(validate_forcing(h));
+  h->have_forcing = true;
+  h->state_set = false;
+  return SVN_OK;
+}
+
+int step_impl(svn_handle* h, double dt, double tol, svn_stats* st) {
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = h->stream;
+  const Layout& g = h->g0;
+  st->status = SVN_OK;
+  TRY(precompute(h, dt));
+  if (!(tol > 0.0)) return fail(h, SVN_ERR_ARG, "tol must be positive");
+  const Phys ph = make_phys(h, g, dt);
+  // reference residual: the plain previous-step start v^n
+  launch_unpack_nodes(s, g, h->in_vold, h->vt);
+  CKL();
+  TRY(residual(h, h->vt, h->R, &st->res0));
+  if (!h->state_set) {
+    CK(cudaMemcpyAsync(h->v, h->vt, sizeof(double2) * g.plane, cudaMemcpyDeviceToDevice, s));
+    launch_pi_init(s, g, ph, h->v, h->pi);
+    CKL();
+  }
+  h->state_set = false;   // a later step restarts from its own v^n unless set_state is called again
+  double phi0, scale0;
+  {
+    const double a0 = 0.0;
+    TRY(energy(h, h->v, h->v, &a0, 1, &phi0, &scale0));
+  }
+  const svn_params& p = h->prm;
+  for (int it = 0;; ++it) {
+    double r;
+    TRY(residual(h, h->v, h->R, &r));
+    st->res_hist[it] = r;
+    st->newton_iters = it;
+    st->res_final = r;
+    st->rel_res_final = st->res0 > 0 ? r / st->res0 : 0.0;
+    if (!std::isfinite(r)) return fail(h, SVN_ERR_NONFINITE, "non-finite residual norm at Newton iteration %d", it);
+    if (r <= tol * st->res0 || r == 0.0) break;
+    if (it >= p.max_newton)
+      return fail(h, SVN_ERR_NO_CONVERGENCE, "no convergence in %d Newton iterations (rel-res %.3e)", it,
+                  st->rel_res_final);
+    TRY(linearize(h, h->v, h->pi));
+    launch_neg_copy(s, g, h->R, h->rhs);
+    CKL();
+    int kits = 0;
+    double eta = p.krylov_rtol;
+    if (p.eisenstat_walker && it > 0) {
+      // Eisenstat-Walker choice 2: eta = 0.9 (r / r_prev)^2, safeguarded
+      const double ratio = r / st->res_hist[it - 1];
+      eta = std::min(0.5, std::max(p.krylov_rtol, 0.9 * ratio * ratio));
+    } else if (p.eisenstat_walker) {
+      eta = 0.5;
+    }
+    TRY(fgmres(h, h->rhs, h->dv, eta, p.max_krylov, &kits));
+    st->krylov_per_newton[it] = kits;
+    st->krylov_iters_total += kits;
+    // backtracking on Phi (Section 5.1)
+    double alpha = 1.0, phi1 = 0.0, scale1 = 0.0;
+    bool ok = false;
+    for (int k = 0; k <= p.max_halvings; ++k) {
+      TRY(energy(h, h->v, h->dv, &alpha, 1, &phi1, &scale1));
+      if (phi1 < phi0) {
+        ok = true;
+      } else if (std::fabs(phi1 - phi0) <= p.ls_floor * scale0) {
+        launch_axpby_to(s, g, h->v, alpha, h->dv, h->vt);
+        CKL();
+        double rn;
+        TRY(residual(h, h->vt, h->w, &rn));
+        ok = rn < r;
+      }
+      if (ok) break;
+      st->halvings_total += 1;
+      alpha *= 0.5;
+    }
+    if (!ok) return fail(h, SVN_ERR_LINESEARCH, "line search failed after %d halvings", p.max_halvings);
+    st->alpha_hist[it] = alpha;
+    launch_dual_update(s, g, ph, alpha, h->v, h->dv, h->pi);
+    launch_axpy(s, g, alpha, h->dv, h->v);
+    CKL();
+    phi0 = phi1;
+    scale0 = scale1;
+  }
+  CK(cudaStreamSynchronize(s));
+  st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return SVN_OK;
+}
+
+int ensure_pi_scratch(svn_handle* h) {
+  if (!h->pi_scratch) TRY(dalloc(h, &h->pi_scratch, 12 * (size_t)h->g0.plane));
+  return SVN_OK;
+}
+
+}  // namespace
+
+// ============================== C ABI ==============================================
+
+extern "C" {
+
+int svn_default_params(svn_params* p) {
+  if (!p) return SVN_ERR_ARG;
+  memset(p, 0, sizeof(*p));
+  p->rho_ice = 900.0; p->rho_a = 1.3; p->rho_o = 1026.0; p->Ca = 1.2e-3; p->Co = 5.5e-3;
+  p->f_c = 1.46e-4; p->Pstar = 27500.0; p->C = 20.0; p->e = 2.0; p->delta_min = 2e-9;
+  p->max_newton = 200;
+  p->max_halvings = 30;
+  p->ls_floor = 1e-13;
+  p->krylov_rtol = 1e-6;
+  p->restart = 30;
+  p->max_krylov = 600;
+  p->precision = SVN_FP64;
+  p->cheb_degree = 3;
+  p->cheb_lo = 0.1;
+  p->coarse_N = 8;
+  p->eisenstat_walker = 0;
+  p->learned = 0;
+  return SVN_OK;
+}
+
+int svn_create(const svn_grid* g, const svn_params* p, void* cuda_stream, svn_handle** out) {
+  if (!out) return SVN_ERR_ARG;
+  *out = nullptr;
+  svn_handle* h = new (std::nothrow) svn_handle();
+  if (!h) return SVN_ERR_OOM;
+  int rc = create_impl(h, g, p, cuda_stream);
+  if (rc != SVN_OK) {
+    // keep the handle so the caller can read the message; it owns nothing usable
+    destroy_impl(h);
+  }
+  *out = h;
+  return rc;
+}
+
+int svn_destroy(svn_handle* h) {
+  if (!h) return SVN_ERR_ARG;
+  destroy_impl(h);
+  delete h;
+  return SVN_OK;
+}
+
+const char* svn_last_error(const svn_handle* h) { return h ? h->err.c_str() : "NULL handle"; }
+
+int svn_set_forcing(svn_handle* h, const double* hc, const double* A, const double* wind, const double* ocean,
+                    const double* v_old) {
+  if (!h) return SVN_ERR_ARG;
+  return set_forcing_impl(h, hc, A, wind, ocean, v_old, false);
+}
+
+int svn_set_forcing_host(svn_handle* h, const double* hc, const double* A, const double* wind, const double* ocean,
+                         const double* v_old) {
+  if (!h) return SVN_ERR_ARG;
+  return set_forcing_impl(h, hc, A, wind, ocean, v_old, true);
+}
+
+static int step_common(svn_handle* h, double dt, double tol, double* out_v, svn_stats* stats, bool host) {
+  if (!h) return SVN_ERR_ARG;
+  svn_stats local;
+  svn_stats* st = stats ? stats : &local;
+  memset(st, 0, sizeof(*st));
+  int rc = step_impl(h, dt, tol, st);
+  st->status = rc;
+  if (out_v && h->v) {
+    const Layout& g = h->g0;
+    const size_t nv = 2 * (size_t)(g.N + 1) * (g.N + 1);
+    if (host) {
+      double* tmp = (double*)h->rhs;   // scratch of 2 * plane >= nv doubles
+      launch_pack_nodes(h->stream, g, h->v, tmp);
+      cudaMemcpyAsync(out_v, tmp, sizeof(double) * nv, cudaMemcpyDeviceToHost, h->stream);
+      cudaStreamSynchronize(h->stream);
+    } else {
+      launch_pack_nodes(h->stream, g, h->v, out_v);
+      cudaStreamSynchronize(h->stream);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess && rc == SVN_OK) rc = fail(h, SVN_ERR_CUDA, "output copy: %s", cudaGetErrorString(e));
+  }
+  return rc;
+}
+
+int svn_step(svn_handle* h, double dt, double tol, double* out_v, svn_stats* stats) {
+  return step_common(h, dt, tol, out_v, stats, false);
+}
+
+int svn_step_host(svn_handle* h, double dt, double tol, double* out_v, svn_stats* stats) {
+  return step_common(h, dt, tol, out_v, stats, true);
+}
+
+int svn_get_state(svn_handle* h, double* v, double* pi) {
+  if (!h || !v || !pi) return SVN_ERR_ARG;
+  launch_pack_nodes(h->stream, h->g0, h->v, v);
+  launch_pack_pi(h->stream, h->g0, h->pi, pi);
+  CKL();
+  CK(cudaStreamSynchronize(h->stream));
+  return SVN_OK;
+}
+
+int svn_set_state(svn_handle* h, const double* v, const double* pi) {
+  if (!h || !v || !pi) return SVN_ERR_ARG;
+  launch_unpack_nodes(h->stream, h->g0, v, h->v);
+  launch_unpack_pi(h->stream, h->g0, pi, h->pi);
+  CKL();
+  h->state_set = true;
+  return SVN_OK;
+}
+
+int svn_residual(svn_handle* h, double dt, const double* v, double* R, double* norm) {
+  if (!h || !v || !R) return SVN_ERR_ARG;
+  TRY(precompute(h, dt));
+  launch_unpack_nodes(h->stream, h->g0, v, h->vt);
+  CKL();
+  double nrm;
+  TRY(residual(h, h->vt, h->w, &nrm));
+  launch_pack_nodes(h->stream, h->g0, h->w, R);
+  CKL();
+  CK(cudaStreamSynchronize(h->stream));
+  if (norm) *norm = nrm;
+  return SVN_OK;
+}
+
+int svn_energy(svn_handle* h, double dt, const double* v, const double* dv, const double* alphas, int k, double* phi,
+               double* scale) {
+  if (!h || !v || !dv || !alphas || !phi) return SVN_ERR_ARG;
+  TRY(precompute(h, dt));
+  launch_unpack_nodes(h->stream, h->g0, v, h->vt);
+  launch_unpack_nodes(h->stream, h->g0, dv, h->w);
+  CKL();
+  return energy(h, h->vt, h->w, alphas, k, phi, scale);
+}
+
+int svn_linearize(svn_handle* h, double dt, const double* v, const double* pi) {
+  if (!h || !v || !pi) return SVN_ERR_ARG;
+  TRY(precompute(h, dt));
+  TRY(ensure_pi_scratch(h));
+  launch_unpack_nodes(h->stream, h->g0, v, h->vt);
+  launch_unpack_pi(h->stream, h->g0, pi, h->pi_scratch);
+  CKL();
+  return linearize(h, h->vt, h->pi_scratch);
+}
+
+int svn_apply(svn_handle* h, int level, const double* x, double* y) {
+  if (!h || !x || !y) return SVN_ERR_ARG;
+  if (level < 0 || level >= (int)h->lv.size()) return fail(h, SVN_ERR_ARG, "level out of range");
+  const Layout& g = h->lv[level].g;
+  launch_unpack_nodes(h->stream, g, x, h->vt);
+  launch_apply<double, double2, double2, double>(h->stream, g, h->lv[level].st64, h->vt, h->w);
+  launch_pack_nodes(h->stream, g, h->w, y);
+  CKL();
+  CK(cudaStreamSynchronize(h->stream));
+  return SVN_OK;
+}
+
+int svn_precondition(svn_handle* h, const double* r, double* z) {
+  if (!h || !r || !z) return SVN_ERR_ARG;
+  const Layout& g = h->g0;
+  launch_unpack_nodes(h->stream, g, r, h->vt);
+  CKL();
+  TRY(precondition(h, h->vt, h->Z));
+  if (h->mixed) launch_cast_f2d(h->stream, g, (const float2*)h->Z, h->w);
+  else CK(cudaMemcpyAsync(h->w, h->Z, sizeof(double2) * g.plane, cudaMemcpyDeviceToDevice, h->stream));
+  launch_pack_nodes(h->stream, g, h->w, z);
+  CKL();
+  CK(cudaStreamSynchronize(h->stream));
+  return SVN_OK;
+}
+
+int svn_krylov_solve(svn_handle* h, const double* b, double* x, double rtol, int* iters) {
+  if (!h || !b || !x) return SVN_ERR_ARG;
+  const Layout& g = h->g0;
+  launch_unpack_nodes(h->stream, g, b, h->rhs);
+  CKL();
+  int its = 0;
+  int rc = fgmres(h, h->rhs, h->dv, rtol, h->prm.max_krylov, &its);
+  if (iters) *iters = its;
+  launch_pack_nodes(h->stream, g, h->dv, x);
+  CK(cudaStreamSynchronize(h->stream));
+  return rc;
+}
+
+int svn_dual_update(svn_handle* h, double dt, const double* v, const double* dv, double alpha, double* pi) {
+  if (!h || !v || !dv || !pi) return SVN_ERR_ARG;
+  TRY(precompute(h, dt));
+  TRY(ensure_pi_scratch(h));
+  const Layout& g = h->g0;
+  launch_unpack_nodes(h->stream, g, v, h->vt);
+  launch_unpack_nodes(h->stream, g, dv, h->w);
+  launch_unpack_pi(h->stream, g, pi, h->pi_scratch);
+  launch_dual_update(h->stream, g, make_phys(h, g, dt), alpha, h->vt, h->w, h->pi_scratch);
+  launch_pack_pi(h->stream, g, h->pi_scratch, pi);
+  CKL();
+  CK(cudaStreamSynchronize(h->stream));
+  return SVN_OK;
+}
+
+}  // extern "C"

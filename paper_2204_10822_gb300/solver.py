@@ -1,0 +1,168 @@
+"""Thin Python binding of the svN C ABI (argument marshalling only).
+
+Device calls take CUDA float64 tensors; ``*_host`` calls take NumPy arrays.
+Array layouts are those of ``include/svn.h``:
+  cells (N, N) [j, i]; node vectors (N+1, N+1, 2) [j, i, k];
+  dual state (N, N, 4, 3) [j, i, q, c].
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import capi
+
+
+class SvnError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s: %s" % (capi.STATUS.get(code, code), msg))
+        self.code = code
+        self.status = capi.STATUS.get(code, str(code))
+
+
+def default_params(**overrides) -> capi.SvnParams:
+    p = capi.SvnParams()
+    capi.lib().svn_default_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        if k == "precision" and isinstance(v, str):
+            v = {"fp64": capi.SVN_FP64, "mixed": capi.SVN_MIXED}[v]
+        setattr(p, k, v)
+    return p
+
+
+def _ptr(t) -> int:
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
+        raise TypeError("expected a contiguous CUDA float64 tensor")
+    return t.data_ptr()
+
+
+def _hptr(a) -> int:
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a.ctypes.data, a
+
+
+class Solver:
+    """One svN solver instance for an N x N grid of side L on the current device."""
+
+    def __init__(self, N: int, L: float = 512e3, stream=None, **params):
+        import torch
+        self.N, self.L = int(N), float(L)
+        self.lib = capi.lib()
+        self.params = default_params(**params)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        g = capi.SvnGrid(self.N, self.L)
+        h = ctypes.c_void_p()
+        rc = self.lib.svn_create(ctypes.byref(g), ctypes.byref(self.params),
+                                 ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        self.h = h
+        if rc != 0:
+            msg = self.lib.svn_last_error(h).decode() if h.value else ""
+            if h.value:
+                self.lib.svn_destroy(h)
+            self.h = None
+            raise SvnError(rc, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.svn_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int):
+        if rc != 0:
+            raise SvnError(rc, self.lib.svn_last_error(self.h).decode())
+
+    # -- shapes --------------------------------------------------------------
+    @property
+    def node_shape(self):
+        return (self.N + 1, self.N + 1, 2)
+
+    @property
+    def pi_shape(self):
+        return (self.N, self.N, 4, 3)
+
+    def _vec(self):
+        import torch
+        return torch.zeros(self.node_shape, dtype=torch.float64, device="cuda")
+
+    # -- step ----------------------------------------------------------------
+    def set_forcing(self, h, A, wind, ocean, v_old):
+        self._check(self.lib.svn_set_forcing(self.h, _ptr(h), _ptr(A), _ptr(wind), _ptr(ocean), _ptr(v_old)))
+
+    def set_forcing_host(self, h, A, wind, ocean, v_old):
+        keep = [_hptr(x) for x in (h, A, wind, ocean, v_old)]
+        self._check(self.lib.svn_set_forcing_host(self.h, *[k[0] for k in keep]))
+
+    def step(self, dt: float, tol: float, out=None, raise_on_error: bool = True):
+        out = self._vec() if out is None else out
+        st = capi.SvnStats()
+        rc = self.lib.svn_step(self.h, dt, tol, _ptr(out), ctypes.byref(st))
+        if rc != 0 and raise_on_error:
+            self._check(rc)
+        return out, st.to_dict()
+
+    def step_host(self, dt: float, tol: float, out: np.ndarray | None = None, raise_on_error: bool = True):
+        out = np.zeros(self.node_shape) if out is None else out
+        st = capi.SvnStats()
+        rc = self.lib.svn_step_host(self.h, dt, tol, out.ctypes.data, ctypes.byref(st))
+        if rc != 0 and raise_on_error:
+            self._check(rc)
+        return out, st.to_dict()
+
+    def get_state(self):
+        import torch
+        v = self._vec()
+        pi = torch.zeros(self.pi_shape, dtype=torch.float64, device="cuda")
+        self._check(self.lib.svn_get_state(self.h, _ptr(v), _ptr(pi)))
+        return v, pi
+
+    def set_state(self, v, pi):
+        self._check(self.lib.svn_set_state(self.h, _ptr(v), _ptr(pi)))
+
+    # -- hot-path components ---------------------------------------------------
+    def residual(self, dt: float, v):
+        R = self._vec()
+        nrm = ctypes.c_double()
+        self._check(self.lib.svn_residual(self.h, dt, _ptr(v), _ptr(R), ctypes.byref(nrm)))
+        return R, nrm.value
+
+    def energy(self, dt: float, v, dv, alphas):
+        k = len(alphas)
+        al = (ctypes.c_double * k)(*alphas)
+        phi = (ctypes.c_double * k)()
+        scale = ctypes.c_double()
+        self._check(self.lib.svn_energy(self.h, dt, _ptr(v), _ptr(dv), al, k, phi, ctypes.byref(scale)))
+        return list(phi), scale.value
+
+    def linearize(self, dt: float, v, pi):
+        self._check(self.lib.svn_linearize(self.h, dt, _ptr(v), _ptr(pi)))
+
+    def apply(self, x, level: int = 0):
+        import torch
+        y = torch.zeros_like(x)
+        self._check(self.lib.svn_apply(self.h, level, _ptr(x), _ptr(y)))
+        return y
+
+    def precondition(self, r):
+        import torch
+        z = torch.zeros_like(r)
+        self._check(self.lib.svn_precondition(self.h, _ptr(r), _ptr(z)))
+        return z
+
+    def krylov_solve(self, b, rtol: float):
+        import torch
+        x = torch.zeros_like(b)
+        its = ctypes.c_int()
+        self._check(self.lib.svn_krylov_solve(self.h, _ptr(b), _ptr(x), rtol, ctypes.byref(its)))
+        return x, its.value
+
+    def dual_update(self, dt: float, v, dv, alpha: float, pi):
+        self._check(self.lib.svn_dual_update(self.h, dt, _ptr(v), _ptr(dv), alpha, _ptr(pi)))
+        return pi
