@@ -177,6 +177,29 @@ int svn_krylov_solve(svn_handle* h, const double* b, double* x, double rtol, int
 int svn_dual_update(svn_handle* h, double dt, const double* v, const double* dv,
                     double alpha, double* pi);
 
+/* ---- Instrumentation (no counterpart in the paper): CUDA-event timing of
+ * one kernel class on the handle's stream, for roofline reporting. ---- */
+enum svn_kernel_class {
+  SVN_K_APPLY = 0,     /* FP64 outer Jacobian apply (stencil form) */
+  SVN_K_CHEB = 1,      /* Chebyshev-Jacobi smoothing sweeps, all levels */
+  SVN_K_MULTIDOT = 2,  /* FGMRES multi-dot (Arnoldi projections) */
+  SVN_K_UPDATE = 3,    /* FGMRES update + norm */
+  SVN_K_ELEMENT = 4,   /* element matrices of the linearisation */
+  SVN_K_RESIDUAL = 5,  /* nonlinear residual (cells + nodes) */
+  SVN_K_ENERGY = 6,    /* energy evaluation */
+  SVN_K_DUAL = 7,      /* dual update */
+  SVN_K_RAP = 8,       /* Galerkin coarse operators */
+  SVN_K_VCYCLE = 9,    /* one whole V-cycle (all of its kernels) */
+  SVN_K_COUNT = 10
+};
+/* enable = 1 resets the totals and starts recording; 0 stops. */
+int svn_profile(svn_handle* h, int enable);
+/* Total milliseconds and number of recorded launches of one class since the
+ * last svn_profile(h, 1); synchronises the handle's stream. */
+int svn_profile_read(svn_handle* h, int kclass, double* ms_total, long long* launches);
+/* Kernel launches issued by this library in this process so far. */
+unsigned long long svn_kernel_launches(void);
+
 #ifdef __cplusplus
 }
 #endif

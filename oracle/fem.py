@@ -185,6 +185,26 @@ class Step:
         return np.sqrt(self.c.delta_min ** 2 + 2.0 * np.sum(t * t, axis=-1))
 
     # -- energy (Eq. "energy") -------------------------------------------
+    def energy_terms(self, v):
+        """The four terms of the integrand of Phi_h at every qp, times the weight.
+
+        (rho H |v|^2 / 2, (-rho H v^n + dt cor - dt tau_atm) . v,
+         dt P/2 (Delta - tr eps), dt Co rho_o |v_o - v|^3 / 3), each (N, N, 4).
+        """
+        m, c, dt = self.mesh, self.c, self.dt
+        ve = m.gather(v)
+        vq = m.at_qp(ve)
+        t = m.tau_at_qp(ve)
+        tr = m.div_at_qp(ve)
+        Dl = self.delta(t)
+        nw = np.linalg.norm(self.vo_q - vq, axis=-1)
+        rhoH = self.rhoH[..., None]
+        P = self.P[..., None]
+        return (m.w * 0.5 * rhoH * np.sum(vq * vq, axis=-1),
+                m.w * np.sum((-rhoH[..., None] * self.vn_q + dt * (self.cor - self.tau_atm)) * vq, axis=-1),
+                m.w * dt * 0.5 * P * (Dl - tr),
+                m.w * dt * c.Co * c.rho_o * nw ** 3 / 3.0)
+
     def energy_density(self, v):
         """Per-quadrature-point integrand of Phi_h times the weight, (N, N, 4)."""
         m, c, dt = self.mesh, self.c, self.dt
@@ -208,8 +228,8 @@ class Step:
         return math.fsum(self.energy_density(v).ravel())
 
     def energy_scale(self, v):
-        """Sum of |contributions|: the rounding scale of Phi_h(v)."""
-        return math.fsum(np.abs(self.energy_density(v)).ravel())
+        """Sum over qp of |each term|: the rounding scale of Phi_h(v)."""
+        return math.fsum(sum(np.abs(t) for t in self.energy_terms(v)).ravel())
 
     # -- residual (Eqs. "Av=F", "A", "F", "sigma") --------------------------
     def residual(self, v):

@@ -69,7 +69,13 @@ _SIGS = {
     "svn_precondition": (c_int, [c_void_p, c_void_p, c_void_p]),
     "svn_krylov_solve": (c_int, [c_void_p, c_void_p, c_void_p, c_double, ctypes.POINTER(c_int)]),
     "svn_dual_update": (c_int, [c_void_p, c_double, c_void_p, c_void_p, c_double, c_void_p]),
+    "svn_profile": (c_int, [c_void_p, c_int]),
+    "svn_profile_read": (c_int, [c_void_p, c_int, P_double, ctypes.POINTER(ctypes.c_longlong)]),
+    "svn_kernel_launches": (ctypes.c_ulonglong, []),
 }
+
+KCLASS = {"apply": 0, "cheb": 1, "multidot": 2, "update": 3, "element": 4, "residual": 5, "energy": 6,
+          "dual": 7, "rap": 8, "vcycle": 9}
 
 _lib = None
 

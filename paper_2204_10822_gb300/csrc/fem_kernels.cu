@@ -555,11 +555,13 @@ const dim3 kNodeBlock(32, 8);
 void launch_precompute(cudaStream_t s, const Layout& g, double dt, const PhysConst& pc, const double* hcell,
                        const double* A, const double* wind, const double* ocean, const double* vold, double* P,
                        double* rhoH, double* fq, double* voq) {
+  note_launch();
   k_precompute<<<cell_grid(g, kCellBlock), kCellBlock, 0, s>>>(g, dt, pc, hcell, A, wind, ocean, vold, P, rhoH,
                                                               fq, voq);
 }
 
 void launch_pi_init(cudaStream_t s, const Layout& g, const Phys& ph, const double2* v, double* pi) {
+  note_launch();
   k_pi_init<<<cell_grid(g, kCellBlock), kCellBlock, 0, s>>>(g, ph, v, pi);
 }
 
@@ -571,7 +573,9 @@ int residual_partials(const Layout& g) {
 void launch_residual(cudaStream_t s, const Layout& g, const Phys& ph, const double2* v, const double* P,
                      const double* rhoH, const double* fq, const double* voq, double* eb, double2* R,
                      double* partial) {
+  note_launch();
   k_residual_cells<<<cell_grid(g, kCellBlock), kCellBlock, 0, s>>>(g, ph, v, P, rhoH, fq, voq, eb);
+  note_launch();
   k_residual_nodes<<<node_grid(g, kNodeBlock), kNodeBlock, 0, s>>>(g, eb, R, partial);
 }
 
@@ -585,13 +589,16 @@ void launch_energy(cudaStream_t s, const Layout& g, const Phys& ph, int k, const
                    double* partial, double* out) {
   dim3 gr = cell_grid(g, kCellBlock);
   const int nb = gr.x * gr.y;
+  note_launch();
   k_energy_cells<<<gr, kCellBlock, 0, s>>>(g, ph, k, al, v, dv, P, rhoH, fq, voq, partial, nb);
+  note_launch();
   k_energy_final<<<1, 1024, 0, s>>>(k, partial, nb, out);
 }
 
 template <typename TE>
 void launch_element_matrices(cudaStream_t s, const Layout& g, const Phys& ph, const double2* v, const double* pi,
                              const double* P, const double* rhoH, const double* voq, TE* ke, float* qcoef) {
+  note_launch();
   k_element_matrices<TE><<<cell_grid(g, kCellBlock), kCellBlock, 0, s>>>(g, ph, v, pi, P, rhoH, voq, ke, qcoef);
 }
 template void launch_element_matrices<double>(cudaStream_t, const Layout&, const Phys&, const double2*,
@@ -600,12 +607,14 @@ template void launch_element_matrices<double>(cudaStream_t, const Layout&, const
 
 template <typename TE, typename TS>
 void launch_stencil_from_elements(cudaStream_t s, const Layout& g, const TE* ke, TS* st) {
+  note_launch();
   k_stencil_from_elements<TE, TS><<<node_grid(g, kNodeBlock), kNodeBlock, 0, s>>>(g, ke, st);
 }
 template void launch_stencil_from_elements<double, double>(cudaStream_t, const Layout&, const double*, double*);
 
 void launch_dual_update(cudaStream_t s, const Layout& g, const Phys& ph, double alpha, const double2* v,
                         const double2* dv, double* pi) {
+  note_launch();
   k_dual_update<<<cell_grid(g, kCellBlock), kCellBlock, 0, s>>>(g, ph, alpha, v, dv, pi);
 }
 

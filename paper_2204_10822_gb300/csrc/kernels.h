@@ -6,6 +6,10 @@
 namespace svn {
 
 constexpr int MAX_ALPHA = 8;
+
+// Process-wide count of kernel launches issued by this library.
+void note_launch();
+unsigned long long launches_issued();
 struct AlphaSet {
   double a[MAX_ALPHA];
 };

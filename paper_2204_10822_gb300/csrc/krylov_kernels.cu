@@ -2,9 +2,15 @@
 // pieces (one-pass multi-dot, one-pass update + norm), FP64 throughout.
 // Reductions are deterministic: per-warp partials, then a fixed-order final
 // reduction.
+#include <atomic>
+
 #include "kernels.h"
 
 namespace svn {
+
+static std::atomic<unsigned long long> g_launches{0};
+void note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+unsigned long long launches_issued() { return g_launches.load(std::memory_order_relaxed); }
 
 namespace {
 
@@ -254,68 +260,86 @@ int reduce_blocks(long long n) { return (int)flat_blocks(n); }
 int krylov_blocks(const Layout& g) { return (int)((g.plane + 32 * EPT - 1) / (32 * EPT)); }
 
 void launch_sum_final(cudaStream_t s, const double* partial, int n, double* out) {
+  note_launch();
   k_sum_final<<<1, 1024, 0, s>>>(partial, n, out);
 }
 void launch_unpack_nodes(cudaStream_t s, const Layout& g, const double* src, double2* dst) {
   dim3 gr((g.ld + kBlk.x - 1) / kBlk.x, (g.n1 + kBlk.y - 1) / kBlk.y);
+  note_launch();
   k_unpack_nodes<<<gr, kBlk, 0, s>>>(g, src, dst);
 }
 void launch_pack_nodes(cudaStream_t s, const Layout& g, const double2* src, double* dst) {
+  note_launch();
   k_pack_nodes<<<ngrid(g), kBlk, 0, s>>>(g, src, dst);
 }
 void launch_unpack_pi(cudaStream_t s, const Layout& g, const double* src, double* pi) {
+  note_launch();
   k_unpack_pi<<<cgrid(g), kBlk, 0, s>>>(g, src, pi);
 }
 void launch_pack_pi(cudaStream_t s, const Layout& g, const double* pi, double* dst) {
+  note_launch();
   k_pack_pi<<<cgrid(g), kBlk, 0, s>>>(g, pi, dst);
 }
 void launch_norm2_partial(cudaStream_t s, const Layout& g, const double2* x, double* partial) {
+  note_launch();
   k_norm2_partial<<<flat_blocks(g.plane), 256, 0, s>>>(g.plane, x, partial);
 }
 void launch_scale_copy(cudaStream_t s, const Layout& g, const double2* x, const double* num, const double* den,
                        double2* y) {
+  note_launch();
   k_scale_copy<<<flat_blocks(g.plane), 256, 0, s>>>(g.plane, x, num, den, y);
 }
 void launch_axpy(cudaStream_t s, const Layout& g, double a, const double2* x, double2* y) {
+  note_launch();
   k_axpy<<<flat_blocks(g.plane), 256, 0, s>>>(g.plane, a, x, y);
 }
 void launch_axpby_to(cudaStream_t s, const Layout& g, const double2* x, double a, const double2* d, double2* y) {
+  note_launch();
   k_axpby_to<<<flat_blocks(g.plane), 256, 0, s>>>(g.plane, x, a, d, y);
 }
 void launch_scale_to(cudaStream_t s, const Layout& g, double a, const double2* x, double2* y) {
+  note_launch();
   k_scale_to<<<flat_blocks(g.plane), 256, 0, s>>>(g.plane, a, x, y);
 }
 void launch_validate(cudaStream_t s, long long ncell, long long nvec, const double* h, const double* A,
                      const double* wind, const double* ocean, const double* vold, int* counts) {
+  note_launch();
   k_validate<<<flat_blocks(nvec), 256, 0, s>>>(ncell, nvec, h, A, wind, ocean, vold, counts);
 }
 void launch_neg_copy(cudaStream_t s, const Layout& g, const double2* x, double2* y) {
+  note_launch();
   k_neg_copy<<<flat_blocks(g.plane), 256, 0, s>>>(g.plane, x, y);
 }
 void launch_cast_d2f(cudaStream_t s, const Layout& g, const double2* x, float2* y) {
+  note_launch();
   k_cast_d2f<<<flat_blocks(g.plane), 256, 0, s>>>(g.plane, x, y);
 }
 void launch_cast_f2d(cudaStream_t s, const Layout& g, const float2* x, double2* y) {
+  note_launch();
   k_cast_f2d<<<flat_blocks(g.plane), 256, 0, s>>>(g.plane, x, y);
 }
 void launch_multidot(cudaStream_t s, const Layout& g, const double2* V, long long vstride, int m, const double2* w,
                      double* partial, int nwarps) {
   const long long threads = (long long)nwarps * 32;
+  note_launch();
   k_multidot<<<(unsigned)((threads + ARN_THREADS - 1) / ARN_THREADS), ARN_THREADS, 0, s>>>(g.plane, V, vstride, m, w,
                                                                                           partial, nwarps);
 }
 void launch_multidot_final(cudaStream_t s, const double* partial, int nwarps, int m, double* h, int accumulate) {
+  note_launch();
   k_multidot_final<<<m, 1024, 0, s>>>(partial, nwarps, h, accumulate);
 }
 void launch_update_norm(cudaStream_t s, const Layout& g, const double2* V, long long vstride, int m, const double* h,
                         double2* w, double* partial, int nwarps) {
   const long long threads = (long long)nwarps * 32;
+  note_launch();
   k_update_norm<<<(unsigned)((threads + ARN_THREADS - 1) / ARN_THREADS), ARN_THREADS, 0, s>>>(g.plane, V, vstride, m,
                                                                                              h, w, partial, nwarps);
 }
 template <typename TZ>
 void launch_lincomb(cudaStream_t s, const Layout& g, const TZ* Z, long long zstride, int m, const double* y,
                     double2* x) {
+  note_launch();
   k_lincomb<TZ><<<flat_blocks(g.plane), 256, 0, s>>>(g.plane, Z, zstride, m, y, x);
 }
 template void launch_lincomb<double2>(cudaStream_t, const Layout&, const double2*, long long, int, const double*,

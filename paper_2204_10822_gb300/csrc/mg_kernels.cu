@@ -440,6 +440,7 @@ static inline dim3 ngrid(const Layout& g) { return dim3((g.n1 + kBlk.x - 1) / kB
 
 template <typename TS, typename TX, typename TY, typename TA>
 void launch_apply(cudaStream_t s, const Layout& g, const TS* st, const TX* x, TY* y) {
+  note_launch();
   k_apply<TS, TX, TY, TA><<<ngrid(g), kBlk, 0, s>>>(g, st, x, y);
 }
 template void launch_apply<double, double2, double2, double>(cudaStream_t, const Layout&, const double*,
@@ -453,45 +454,53 @@ template void launch_apply<__nv_bfloat16, float2, float2, float>(cudaStream_t, c
 
 template <typename TS, typename TV>
 void launch_residual_stencil(cudaStream_t s, const Layout& g, const TS* st, const TV* x, const TV* b, TV* r) {
+  note_launch();
   k_residual_stencil<TS, TV><<<ngrid(g), kBlk, 0, s>>>(g, st, x, b, r);
 }
 
 template <typename TS, typename TD>
 int launch_dinv_gershgorin(cudaStream_t s, const Layout& g, const TS* st, TD* dinv, double* partial) {
   dim3 gr = ngrid(g);
+  note_launch();
   k_dinv_gershgorin<TS, TD><<<gr, kBlk, 0, s>>>(g, st, dinv, partial);
   return gr.x * gr.y;
 }
 
 void launch_max_final(cudaStream_t s, const double* partial, int n, double* out) {
+  note_launch();
   k_max_final<<<1, 1024, 0, s>>>(partial, n, out);
 }
 
 template <typename TS, typename TD, typename TV>
 void launch_cheb_zero_start(cudaStream_t s, const Layout& g, const TD* dinv, const double* lmax, double lo,
                             const TV* b, TV* x, TV* d) {
+  note_launch();
   k_cheb_zero_start<TD, TV><<<ngrid(g), kBlk, 0, s>>>(g, dinv, lmax, lo, b, x, d);
 }
 
 template <typename TS, typename TD, typename TV>
 void launch_cheb_sweep(cudaStream_t s, const Layout& g, const TS* st, const TD* dinv, const double* lmax, double lo,
                        int step, const TV* xin, TV* xout, TV* d, const TV* b) {
+  note_launch();
   k_cheb_sweep<TS, TD, TV><<<ngrid(g), kBlk, 0, s>>>(g, st, dinv, lmax, lo, step, xin, xout, d, b);
 }
 
 template <typename TV>
 void launch_restrict(cudaStream_t s, const Layout& gf, const Layout& gc, const TV* rf, TV* bc) {
+  note_launch();
   k_restrict<TV><<<ngrid(gc), kBlk, 0, s>>>(gf, gc, rf, bc);
 }
 
 template <typename TV>
 void launch_prolong_add(cudaStream_t s, const Layout& gf, const Layout& gc, const TV* xc, TV* xf) {
+  note_launch();
   k_prolong_add<TV><<<ngrid(gf), kBlk, 0, s>>>(gf, gc, xc, xf);
 }
 
 template <typename TF, typename TC>
 void launch_rap(cudaStream_t s, const Layout& gf, const Layout& gc, const TF* stf, TC* stc) {
   using TA = typename std::conditional<std::is_same<TF, double>::value, double, float>::type;
+  note_launch();
   k_rap<TA, TF, TC><<<ngrid(gc), kBlk, 0, s>>>(gf, gc, stf, stc);
 }
 
@@ -499,22 +508,26 @@ template <typename TS>
 void launch_coarse_dense(cudaStream_t s, const Layout& g, const TS* st, double* dense) {
   const int m = g.N - 1, n2 = 2 * m * m;
   cudaMemsetAsync(dense, 0, sizeof(double) * (size_t)n2 * n2, s);
+  note_launch();
   k_coarse_dense<TS><<<ngrid(g), kBlk, 0, s>>>(g, st, dense);
 }
 
 void launch_cholesky_inverse(cudaStream_t s, int n, double* a, double* inv, int* info) {
+  note_launch();
   k_cholesky_inverse<<<1, 256, 0, s>>>(n, a, inv, info);
 }
 
 template <typename TV>
 void launch_coarse_solve(cudaStream_t s, const Layout& g, int n2, const double* inv, const TV* b, TV* x) {
   cudaMemsetAsync(x, 0, sizeof(TV) * g.plane, s);
+  note_launch();
   k_coarse_solve<TV><<<(n2 + 127) / 128, 128, 0, s>>>(g, n2, inv, b, x);
 }
 
 template <typename TA, typename TB>
 void launch_convert_stencil(cudaStream_t s, const Layout& g, const TA* a, TB* b) {
   const long long n = (long long)NSTEN * g.plane;
+  note_launch();
   k_convert<TA, TB><<<(unsigned)((n + 255) / 256), 256, 0, s>>>(n, a, b);
 }
 

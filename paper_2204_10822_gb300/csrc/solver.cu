@@ -79,6 +79,17 @@ struct svn_handle {
   double* scal = nullptr;       // device scalars
   double* hostbuf = nullptr;    // pinned host mirror
   size_t hostbuf_len = 0;
+
+  // instrumentation
+  struct ProfRec {
+    int cls;
+    cudaEvent_t a, b;
+  };
+  bool prof_on = false;
+  std::vector<ProfRec> recs;
+  std::vector<cudaEvent_t> pool;
+  double prof_ms[SVN_K_COUNT] = {};
+  long long prof_n[SVN_K_COUNT] = {};
 };
 
 namespace {
@@ -130,6 +141,50 @@ void dfree(T*& p) {
   p = nullptr;
 }
 
+// Records CUDA events around the launches of one kernel class when enabled.
+struct Prof {
+  svn_handle* h;
+  int cls;
+  cudaEvent_t a = nullptr, b = nullptr;
+  static cudaEvent_t ev(svn_handle* h) {
+    if (!h->pool.empty()) {
+      cudaEvent_t e = h->pool.back();
+      h->pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+  }
+  Prof(svn_handle* hh, int c) : h(hh), cls(c) {
+    if (h->prof_on) {
+      a = ev(h);
+      b = ev(h);
+      cudaEventRecord(a, h->stream);
+    }
+  }
+  ~Prof() {
+    if (a) {
+      cudaEventRecord(b, h->stream);
+      h->recs.push_back({cls, a, b});
+    }
+  }
+};
+
+void prof_collect(svn_handle* h) {
+  if (h->recs.empty()) return;
+  cudaStreamSynchronize(h->stream);
+  for (auto& r : h->recs) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, r.a, r.b);
+    h->prof_ms[r.cls] += ms;
+    h->prof_n[r.cls] += 1;
+    h->pool.push_back(r.a);
+    h->pool.push_back(r.b);
+  }
+  h->recs.clear();
+}
+
 Phys make_phys(const svn_handle* h, const Layout& g, double dt) {
   Phys ph;
   const double e = h->prm.e;
@@ -171,7 +226,10 @@ int precompute(svn_handle* h, double dt) {
 
 int residual(svn_handle* h, const double2* v, double2* R, double* norm) {
   const Phys ph = make_phys(h, h->g0, h->cur_dt);
-  launch_residual(h->stream, h->g0, ph, v, h->P, h->rhoH, h->fq, h->voq, h->eb, R, h->partial);
+  {
+    Prof pr(h, SVN_K_RESIDUAL);
+    launch_residual(h->stream, h->g0, ph, v, h->P, h->rhoH, h->fq, h->voq, h->eb, R, h->partial);
+  }
   launch_sum_final(h->stream, h->partial, residual_partials(h->g0), h->scal);
   CKL();
   double s;
@@ -186,7 +244,10 @@ int energy(svn_handle* h, const double2* v, const double2* dv, const double* alp
   const Phys ph = make_phys(h, h->g0, h->cur_dt);
   AlphaSet al{};
   for (int a = 0; a < k; ++a) al.a[a] = alphas[a];
-  launch_energy(h->stream, h->g0, ph, k, al, v, dv, h->P, h->rhoH, h->fq, h->voq, h->partial, h->scal);
+  {
+    Prof pr(h, SVN_K_ENERGY);
+    launch_energy(h->stream, h->g0, ph, k, al, v, dv, h->P, h->rhoH, h->fq, h->voq, h->partial, h->scal);
+  }
   CKL();
   double out[MAX_ALPHA + 1];
   TRY(sync_read(h, h->scal, MAX_ALPHA + 1, out));
@@ -198,11 +259,17 @@ int energy(svn_handle* h, const double2* v, const double2* dv, const double* alp
 int linearize(svn_handle* h, const double2* v, const double* pi) {
   const Phys ph = make_phys(h, h->g0, h->cur_dt);
   cudaStream_t s = h->stream;
-  launch_element_matrices<double>(s, h->g0, ph, v, pi, h->P, h->rhoH, h->voq, h->eb, nullptr);
+  {
+    Prof pr(h, SVN_K_ELEMENT);
+    launch_element_matrices<double>(s, h->g0, ph, v, pi, h->P, h->rhoH, h->voq, h->eb, nullptr);
+  }
   launch_stencil_from_elements<double, double>(s, h->g0, h->eb, h->lv[0].st64);
   CKL();
   const int L = (int)h->lv.size();
-  for (int l = 1; l < L; ++l) launch_rap<double, double>(s, h->lv[l - 1].g, h->lv[l].g, h->lv[l - 1].st64, h->lv[l].st64);
+  for (int l = 1; l < L; ++l) {
+    Prof pr(h, SVN_K_RAP);
+    launch_rap<double, double>(s, h->lv[l - 1].g, h->lv[l].g, h->lv[l - 1].st64, h->lv[l].st64);
+  }
   CKL();
   for (int l = 0; l < L - 1; ++l) {
     Level& lv = h->lv[l];
@@ -251,6 +318,7 @@ void vcycle(svn_handle* h, int l, const TV* b, TV* xout) {
   TV* cur = x0;
   TV* nxt = x1;
   for (int k = 1; k < deg; ++k) {
+    Prof pr(h, SVN_K_CHEB);
     launch_cheb_sweep<TS, TD, TV>(s, lv.g, st, dinv, lv.lmax, lo, k, cur, nxt, d, b);
     std::swap(cur, nxt);
   }
@@ -263,6 +331,7 @@ void vcycle(svn_handle* h, int l, const TV* b, TV* xout) {
   // post-smoothing (same polynomial), the last sweep writing xout when it can
   for (int k = 0; k < deg; ++k) {
     TV* dst = (k == deg - 1 && xout != cur) ? xout : (cur == x0 ? x1 : x0);
+    Prof pr(h, SVN_K_CHEB);
     launch_cheb_sweep<TS, TD, TV>(s, lv.g, st, dinv, lv.lmax, lo, k, cur, dst, d, b);
     cur = dst;
   }
@@ -273,6 +342,7 @@ void vcycle(svn_handle* h, int l, const TV* b, TV* xout) {
 // z = M^-1 r for a level-0 FP64 vector r; z in the V-cycle precision.
 int precondition(svn_handle* h, const double2* r, void* z) {
   Level& l0 = h->lv[0];
+  Prof pr(h, SVN_K_VCYCLE);
   if (h->mixed) {
     launch_cast_d2f(h->stream, l0.g, r, (float2*)l0.b);
     vcycle<__nv_bfloat16, float, float2>(h, 0, (const float2*)l0.b, (float2*)z);
@@ -285,6 +355,7 @@ int precondition(svn_handle* h, const double2* r, void* z) {
 
 // y = K0 z (FP64 outer operator), z in the V-cycle precision.
 void apply_outer(svn_handle* h, const void* z, double2* y) {
+  Prof pr(h, SVN_K_APPLY);
   if (h->mixed)
     launch_apply<double, float2, double2, double>(h->stream, h->g0, h->lv[0].st64, (const float2*)z, y);
   else
@@ -335,12 +406,16 @@ int fgmres(svn_handle* h, const double2* b, double2* x, double rtol, int maxit, 
       double* h1 = h->hbuf;
       double* h2 = h->hbuf + (m + 1);
       double* nr = h->hbuf + 2 * (m + 1);
-      launch_multidot(s, g, h->V, vs, j + 1, h->w, h->partial, nw);
-      launch_multidot_final(s, h->partial, nw, j + 1, h1, 0);
-      launch_update_norm(s, g, h->V, vs, j + 1, h1, h->w, h->partial, nw);
-      launch_multidot(s, g, h->V, vs, j + 1, h->w, h->partial, nw);
-      launch_multidot_final(s, h->partial, nw, j + 1, h2, 0);
-      launch_update_norm(s, g, h->V, vs, j + 1, h2, h->w, h->partial, nw);
+      for (int pass = 0; pass < 2; ++pass) {
+        double* hp = pass == 0 ? h1 : h2;
+        {
+          Prof pr(h, SVN_K_MULTIDOT);
+          launch_multidot(s, g, h->V, vs, j + 1, h->w, h->partial, nw);
+        }
+        launch_multidot_final(s, h->partial, nw, j + 1, hp, 0);
+        Prof pr(h, SVN_K_UPDATE);
+        launch_update_norm(s, g, h->V, vs, j + 1, hp, h->w, h->partial, nw);
+      }
       launch_sum_final(s, h->partial, nw, nr);
       CKL();
       std::vector<double> hh(2 * (m + 1) + 1);
@@ -502,6 +577,13 @@ void destroy_impl(svn_handle* h) {
   dfree(h->V); dfree(h->Z); dfree(h->hbuf); dfree(h->ybuf); dfree(h->partial); dfree(h->scal);
   if (h->hostbuf) cudaFreeHost(h->hostbuf);
   h->hostbuf = nullptr;
+  for (auto& r : h->recs) {
+    h->pool.push_back(r.a);
+    h->pool.push_back(r.b);
+  }
+  h->recs.clear();
+  for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
+  h->pool.clear();
 }
 
 // Validate the device copies of the inputs (counts of bad entries, one read-back).
@@ -611,7 +693,10 @@ int step_impl(svn_handle* h, double dt, double tol, svn_stats* st) {
     }
     if (!ok) return fail(h, SVN_ERR_LINESEARCH, "line search failed after %d halvings", p.max_halvings);
     st->alpha_hist[it] = alpha;
-    launch_dual_update(s, g, ph, alpha, h->v, h->dv, h->pi);
+    {
+      Prof pr(h, SVN_K_DUAL);
+      launch_dual_update(s, g, ph, alpha, h->v, h->dv, h->pi);
+    }
     launch_axpy(s, g, alpha, h->dv, h->v);
     CKL();
     phi0 = phi1;
@@ -826,5 +911,28 @@ int svn_dual_update(svn_handle* h, double dt, const double* v, const double* dv,
   CK(cudaStreamSynchronize(h->stream));
   return SVN_OK;
 }
+
+int svn_profile(svn_handle* h, int enable) {
+  if (!h) return SVN_ERR_ARG;
+  prof_collect(h);
+  if (enable) {
+    for (int c = 0; c < SVN_K_COUNT; ++c) {
+      h->prof_ms[c] = 0.0;
+      h->prof_n[c] = 0;
+    }
+  }
+  h->prof_on = enable != 0;
+  return SVN_OK;
+}
+
+int svn_profile_read(svn_handle* h, int kclass, double* ms_total, long long* launches) {
+  if (!h || kclass < 0 || kclass >= SVN_K_COUNT) return SVN_ERR_ARG;
+  prof_collect(h);
+  if (ms_total) *ms_total = h->prof_ms[kclass];
+  if (launches) *launches = h->prof_n[kclass];
+  return SVN_OK;
+}
+
+unsigned long long svn_kernel_launches(void) { return launches_issued(); }
 
 }  // extern "C"

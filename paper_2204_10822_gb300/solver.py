@@ -163,6 +163,20 @@ class Solver:
         self._check(self.lib.svn_krylov_solve(self.h, _ptr(b), _ptr(x), rtol, ctypes.byref(its)))
         return x, its.value
 
+    # -- instrumentation -------------------------------------------------------
+    def profile(self, enable: bool):
+        self._check(self.lib.svn_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self, kclass: str):
+        ms = ctypes.c_double()
+        n = ctypes.c_longlong()
+        self._check(self.lib.svn_profile_read(self.h, capi.KCLASS[kclass], ctypes.byref(ms), ctypes.byref(n)))
+        return ms.value, n.value
+
+    @staticmethod
+    def kernel_launches() -> int:
+        return int(capi.lib().svn_kernel_launches())
+
     def dual_update(self, dt: float, v, dv, alpha: float, pi):
         self._check(self.lib.svn_dual_update(self.h, dt, _ptr(v), _ptr(dv), alpha, _ptr(pi)))
         return pi

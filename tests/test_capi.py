@@ -14,7 +14,8 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_functions():
     hdr = open(os.path.join(ROOT, "include", "svn.h")).read()
     hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:int|const char\s*\*)\s*(svn_\w+)\s*\(", hdr, flags=re.M)))
+    return sorted(set(re.findall(r"^\s*(?:int|const char\s*\*|unsigned long long)\s*(svn_\w+)\s*\(", hdr,
+                                 flags=re.M)))
 
 
 @pytest.fixture(scope="module")
