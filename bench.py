@@ -1,0 +1,295 @@
+#!/usr/bin/env python
+"""Benchmark of the svN implicit sea-ice step on GB300.
+
+One "step" is one implicit momentum step (1800 s) solved to relative
+residual 1e-8 by the full hot path: residual, linearisation, multigrid-
+preconditioned FGMRES, line search on the energy, dual update.  Workload:
+2048 x 2048 cells (8,396,802 velocity DOF), synthetic seeded fields (GRF ice,
+Rankine-vortex wind, gyre ocean), Delta_min = 2e-9 1/s, mixed precision.
+
+Prints ONE JSON line (rank 0).  `--impl reference` times the FP64 CPU oracle
+(a deliberately slow plain implementation) on a bounded sample instead.
+With torchrun (N > 1) every rank solves an independent replica (no collective
+on the data path); timing is max over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "s/implicit step to rel-res 1e-8 @8.4M DOF (mixed precision)"
+UNIT = "s/step"
+SAMPLE_N = 128        # oracle sample grid for the CPU baseline / reference arm
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=2048)
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--tol", type=float, default=1e-8)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def workload_config(args, N):
+    dof = 2 * (N + 1) ** 2
+    return {"workload": "svN implicit step, %dx%d cells (%d DOF), dt=1800 s, Delta_min=2e-9, "
+                        "GRF ice + Rankine vortex + gyre, tol %.0e" % (N, N, dof, args.tol),
+            "N": N, "dof": dof, "precision": args.precision, "tol": args.tol,
+            "l2": "inputs larger than L2 (level-0 stencil alone %.0f MB)" % (19 * 8 * (N + 1) ** 2 / 1e6),
+            "parallelism": "replicas"}
+
+
+# ---------------------------------------------------------------------------------------
+def oracle_sample(N: int, steps: int, warmup: int) -> dict:
+    """Time the FP64 oracle on the host cores (single thread), in a subprocess."""
+    code = (
+        "import json, os, sys, time; sys.path.insert(0, %r)\n"
+        "import workloads as W\n"
+        "from oracle.newton import newton\n"
+        "p = W.config(2, N=%d)\n"
+        "ts = []\n"
+        "for k in range(%d):\n"
+        "    t = time.perf_counter(); r = newton(p, tol=1e-8); ts.append(time.perf_counter() - t)\n"
+        "print(json.dumps({'times': ts[%d:], 'newton': r.newton_iters}))\n" % (ROOT, N, steps + warmup, warmup))
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline_obj(N_full: int, steps: int = 1, warmup: int = 0) -> dict:
+    res = oracle_sample(SAMPLE_N, steps, warmup)
+    t = statistics.mean(res["times"])
+    scale = (N_full + 1) ** 2 / (SAMPLE_N + 1) ** 2
+    return {"value": t * scale, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": "full oracle step (SuperLU direct solves, %d Newton its) at %dx%d cells, %.2f s, scaled "
+                      "x%.1f by DOF to %dx%d (linear: a lower bound for a direct solver)" % (
+                          res["newton"], SAMPLE_N, SAMPLE_N, t, scale, N_full, N_full)}
+
+
+# ---------------------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.QUERY,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        self.proc.wait()
+        rows = [r.split(", ") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        sm = [float(r[1]) for r in rows if len(r) >= 9 and r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if len(r) >= 9 and r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows if len(r) >= 9 for k in range(4) if r[5 + k].strip() == "Active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# algorithmic bytes per unit (node) of each kernel class; the roofline block
+# reports the class with the largest share of the timed region
+def algorithmic(kclass: str, N: int, mixed: bool, stats: list[dict], restart: int):
+    nodes = (N + 1) ** 2
+    if kclass == "apply":
+        per_node = (8 if mixed else 16) + 16 + 19 * 8      # x (f32|f64) + y f64 + 19 f64 coefficients
+        return per_node * nodes, "hbm"
+    if kclass in ("multidot", "update"):
+        # pass reads (j+1) basis vectors + w (multidot) / + w read+write (update), j per Krylov iteration
+        tot = 0
+        for st in stats:
+            for k in st["krylov_per_newton"]:
+                for it in range(k):
+                    j = it % restart
+                    vecs = (j + 1) + (1 if kclass == "multidot" else 2)
+                    tot += 2 * vecs * 16 * nodes        # CGS2: two passes
+        return tot, "hbm"
+    return None, None
+
+
+def run_ours(args, rank, world):
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2204_10822_gb300 import Solver
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    N = args.N
+    p = W.config(2, N=N)
+    kw = dict(precision=args.precision, eisenstat_walker=1, krylov_rtol=1e-4, max_krylov=600)
+    s = Solver(N, p.L, **kw)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    dev_in = [t(p.h), t(p.A), t(p.wind), t(p.ocean), t(p.v_old)]
+    s.set_forcing(*dev_in)
+    out = torch.zeros((N + 1, N + 1, 2), dtype=torch.float64, device="cuda")
+
+    def barrier():
+        if world > 1:
+            torch.distributed.barrier()
+
+    for _ in range(args.warmup):
+        s.step(p.dt, args.tol, out=out)
+    clocks = ClockSampler(local)
+    if not args.no_clocks:
+        clocks.start()
+    s.profile(True)
+    launches0 = Solver.kernel_launches()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    stats = []
+    for _ in range(args.steps):
+        _, st = s.step(p.dt, args.tol, out=out)
+        stats.append(st)
+    e1.record()
+    torch.cuda.synchronize()
+    barrier()
+    launches = Solver.kernel_launches() - launches0
+    clk = clocks.stop() if not args.no_clocks else {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["not sampled"]}
+    s.profile(False)
+    elapsed = e0.elapsed_time(e1) / 1000.0
+    prof = {k: s.profile_read(k) for k in ("apply", "cheb", "multidot", "update", "element", "residual", "energy",
+                                           "dual", "rap", "vcycle")}
+    tmax = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
+    if world > 1:
+        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
+    tmax = float(tmax.item())
+
+    # end to end through the C ABI with host buffers (pinned), copies inside
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
+        host_in = [pin(x) for x in (p.h, p.A, p.wind, p.ocean, p.v_old)]
+        host_out = torch.zeros((N + 1, N + 1, 2), dtype=torch.float64).pin_memory()
+        hn = [x.numpy() for x in host_in]
+        s.set_forcing_host(*hn)
+        s.step_host(p.dt, args.tol, out=host_out.numpy())
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            s.set_forcing_host(*hn)
+            s.step_host(p.dt, args.tol, out=host_out.numpy())
+        te = time.perf_counter() - t0
+        te_t = torch.tensor([te], dtype=torch.float64, device="cuda")
+        if world > 1:
+            torch.distributed.all_reduce(te_t, op=torch.distributed.ReduceOp.MAX)
+        e2e = {"value": float(te_t.item()) / (args.steps * world), "unit": UNIT,
+               "h2d_bytes_per_step": int(sum(x.numel() * 8 for x in host_in)),
+               "d2h_bytes_per_step": int(host_out.numel() * 8)}
+
+    result = None
+    if rank == 0:
+        dom = max(("apply", "cheb", "multidot", "update", "element", "residual", "energy", "dual", "rap"),
+                  key=lambda k: prof[k][0])
+        roof = None
+        peaks = {}
+        pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        if os.path.exists(pk_path):
+            peaks = json.load(open(pk_path))
+        hbm_peak = peaks.get("hbm_gbs", 6800.0)
+        peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
+        # the headline roofline: the FP64 outer Jacobian apply (the operator of every Krylov iteration)
+        for kc in ("apply",):
+            ms, n = prof[kc]
+            byt, bound = algorithmic(kc, N, args.precision == "mixed", stats, s.params.restart)
+            if n and byt:
+                avg_s = ms / 1000.0 / n
+                ach = byt / avg_s / 1e9
+                roof = {"kernel": "k_apply (FP64 stencil Jacobian apply)", "bound": bound, "achieved": ach,
+                        "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s", "frac": ach / hbm_peak,
+                        "traffic": None, "launches": n, "avg_us": avg_s * 1e6,
+                        "algorithmic_bytes_per_launch": byt}
+        shares = {k: round(prof[k][0] / 1000.0 / elapsed, 4) for k in prof}
+        result = {
+            "metric": METRIC, "value": tmax / (args.steps * world), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1000.0,
+            "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+f32" if args.precision == "mixed" else "f64", "data": "synthetic",
+            "config": workload_config(args, N),
+            "newton_iters": [st["newton_iters"] for st in stats],
+            "krylov_iters": [st["krylov_iters_total"] for st in stats],
+            "rel_res_final": [st["rel_res_final"] for st in stats],
+            "gpu_launches": int(launches), "clocks": clk, "roofline": roof,
+            "kernel_share": shares, "dominant_kernel_class": dom, "e2e": e2e,
+        }
+    return result
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        res = oracle_sample(SAMPLE_N, args.steps, args.warmup)
+        t = statistics.mean(res["times"])
+        scale = (args.N + 1) ** 2 / (SAMPLE_N + 1) ** 2
+        val = t * scale
+        cb = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
+              "sample": "full oracle step at %dx%d cells per timed step (%.2f s), scaled x%.1f by DOF" % (
+                  SAMPLE_N, SAMPLE_N, t, scale)}
+        args.precision = "fp64"
+        line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 1,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1000.0, "higher_is_better": False,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": workload_config(args, args.N), "cpu_baseline": cb,
+                "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+                "gpu_launches": 0}
+        print(json.dumps(line))
+        return 0
+    if world > 1:
+        import torch
+        torch.distributed.init_process_group("nccl")
+    cb = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        cb = cpu_baseline_obj(args.N)
+    res = run_ours(args, rank, world)
+    if rank == 0:
+        res["cpu_baseline"] = cb
+        print(json.dumps(res))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())
