@@ -126,7 +126,7 @@ class ClockSampler:
 def algorithmic(kclass: str, N: int, mixed: bool, stats: list[dict], restart: int):
     nodes = (N + 1) ** 2
     if kclass == "apply":
-        per_node = (8 if mixed else 16) + 16 + 19 * 8      # x (f32|f64) + y f64 + 19 f64 coefficients
+        per_node = 16 + 16 + 19 * 8      # x f64 + y f64 + 19 f64 coefficients
         return per_node * nodes, "hbm"
     if kclass in ("multidot", "update"):
         # pass reads (j+1) basis vectors + w (multidot) / + w read+write (update), j per Krylov iteration
@@ -246,6 +246,8 @@ def run_ours(args, rank, world):
             "newton_iters": [st["newton_iters"] for st in stats],
             "krylov_iters": [st["krylov_iters_total"] for st in stats],
             "rel_res_final": [st["rel_res_final"] for st in stats],
+            "krylov_per_newton": stats[0]["krylov_per_newton"],
+            "alpha_hist": stats[0]["alpha_hist"],
             "gpu_launches": int(launches), "clocks": clk, "roofline": roof,
             "kernel_share": shares, "dominant_kernel_class": dom, "e2e": e2e,
         }

@@ -87,6 +87,10 @@ typedef struct svn_params {
   int coarse_N;             /* coarsest multigrid level has coarse_N cells per side */
   int eisenstat_walker;     /* 1: adapt krylov_rtol per Newton step (timed runs) */
   int learned;              /* 1: try the learned initial guess (svn_learned_load) */
+  int use_graphs;           /* 1: run each V-cycle as one captured CUDA graph */
+  int reorth_always;        /* 1: always two Gram-Schmidt passes; 0: second pass only
+                               when the first cancels more than half of |w|^2 */
+  double ew_eta_max;        /* upper bound of the Eisenstat-Walker forcing term */
 } svn_params;
 
 typedef struct svn_stats {

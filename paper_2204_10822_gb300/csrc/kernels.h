@@ -50,13 +50,17 @@ void launch_residual_stencil(cudaStream_t s, const Layout& g, const TS* st, cons
 template <typename TS, typename TD>
 int launch_dinv_gershgorin(cudaStream_t s, const Layout& g, const TS* st, TD* dinv, double* partial);
 void launch_max_final(cudaStream_t s, const double* partial, int n, double* out);
-// Chebyshev smoothing (Saad Alg. 12.1 on D^-1 A over [lo lmax, lmax]).
+// Chebyshev smoothing (Saad Alg. 12.1 on D^-1 A over [lo lmax, lmax]); the
+// step coefficients are computed on the device from lmax (launch_cheb_coefs).
+template <typename T>
+void launch_cheb_coefs(cudaStream_t s, const double* lmax, double lo, int deg, T* coef);
 template <typename TS, typename TD, typename TV>
-void launch_cheb_zero_start(cudaStream_t s, const Layout& g, const TD* dinv, const double* lmax, double lo,
-                            const TV* b, TV* x, TV* d);
+void launch_cheb_zero_start(cudaStream_t s, const Layout& g, const TD* dinv,
+                            const typename ScalarOf<TV>::type* coef, const TV* b, TV* x, TV* d);
 template <typename TS, typename TD, typename TV>
-void launch_cheb_sweep(cudaStream_t s, const Layout& g, const TS* st, const TD* dinv, const double* lmax,
-                       double lo, int step, const TV* xin, TV* xout, TV* d, const TV* b);
+void launch_cheb_sweep(cudaStream_t s, const Layout& g, const TS* st, const TD* dinv,
+                       const typename ScalarOf<TV>::type* coef, int step, const TV* xin, TV* xout, TV* d,
+                       const TV* b);
 template <typename TV>
 void launch_restrict(cudaStream_t s, const Layout& gf, const Layout& gc, const TV* rf, TV* bc);
 template <typename TV>

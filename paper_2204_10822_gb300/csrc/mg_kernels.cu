@@ -10,9 +10,6 @@
 
 namespace svn {
 
-template <typename V> struct ScalarOf;
-template <> struct ScalarOf<double2> { using type = double; };
-template <> struct ScalarOf<float2> { using type = float; };
 
 template <typename TA, typename TS>
 __device__ __forceinline__ TA ldc(const TS* p) {
@@ -190,16 +187,35 @@ __device__ __forceinline__ ChebCoef cheb_coef(double lmax, double lo) {
   return c;
 }
 
+// Chebyshev step coefficients, once per level after lmax is known:
+// coef[2k] = c1_k, coef[2k+1] = c2_k with d_k = c1_k d_{k-1} + c2_k D^-1 r_k
+// (Saad Alg. 12.1: c1_0 = 0, c2_0 = 1/theta; rho_0 = 1/sigma,
+//  rho_k = 1/(2 sigma - rho_{k-1}), c1_k = rho_k rho_{k-1}, c2_k = 2 rho_k / delta).
+template <typename T>
+__global__ void k_cheb_coefs(const double* __restrict__ lmax, double lo, int deg, T* __restrict__ coef) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  const ChebCoef c = cheb_coef(*lmax, lo);
+  double rho = 1.0 / c.sigma;
+  coef[0] = (T)0;
+  coef[1] = (T)(1.0 / c.theta);
+  for (int k = 1; k < deg; ++k) {
+    const double rn = 1.0 / (2.0 * c.sigma - rho);
+    coef[2 * k] = (T)(rn * rho);
+    coef[2 * k + 1] = (T)(2.0 * rn / c.delta);
+    rho = rn;
+  }
+}
+
 template <typename TD, typename TV>
-__global__ void k_cheb_zero_start(Layout g, const TD* __restrict__ dinv, const double* __restrict__ lmax, double lo,
+__global__ void k_cheb_zero_start(Layout g, const TD* __restrict__ dinv,
+                                  const typename ScalarOf<TV>::type* __restrict__ coef,
                                   const TV* __restrict__ b, TV* __restrict__ x, TV* __restrict__ d) {
   using T = typename ScalarOf<TV>::type;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i > g.N || j > g.N) return;
   const long long n = (long long)j * g.ld + i;
-  const ChebCoef c = cheb_coef(*lmax, lo);
-  const T it = (T)(1.0 / c.theta);
+  const T it = coef[1];
   const TV bb = b[n];
   const T i00 = ldc<T>(dinv + n), i01 = ldc<T>(dinv + g.plane + n), i11 = ldc<T>(dinv + 2 * g.plane + n);
   const TV dd = mk2<TV>(it * (i00 * bb.x + i01 * bb.y), it * (i01 * bb.x + i11 * bb.y));
@@ -209,8 +225,9 @@ __global__ void k_cheb_zero_start(Layout g, const TD* __restrict__ dinv, const d
 
 template <typename TS, typename TD, typename TV>
 __global__ void k_cheb_sweep(Layout g, const TS* __restrict__ st, const TD* __restrict__ dinv,
-                             const double* __restrict__ lmax, double lo, int step, const TV* __restrict__ xin,
-                             TV* __restrict__ xout, TV* __restrict__ d, const TV* __restrict__ b) {
+                             const typename ScalarOf<TV>::type* __restrict__ coef, int step,
+                             const TV* __restrict__ xin, TV* __restrict__ xout, TV* __restrict__ d,
+                             const TV* __restrict__ b) {
   using T = typename ScalarOf<TV>::type;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
@@ -220,28 +237,15 @@ __global__ void k_cheb_sweep(Layout g, const TS* __restrict__ st, const TD* __re
     xout[n] = mk2<TV>(T(0), T(0));
     return;
   }
-  const ChebCoef c = cheb_coef(*lmax, lo);
-  double c1, c2;
-  if (step == 0) {
-    c1 = 0.0;
-    c2 = 1.0 / c.theta;
-  } else {
-    double rho = 1.0 / c.sigma, rn = rho;
-    for (int s = 0; s < step; ++s) {
-      rn = 1.0 / (2.0 * c.sigma - rho);
-      if (s + 1 < step) rho = rn;
-    }
-    c1 = rn * rho;
-    c2 = 2.0 * rn / c.delta;
-  }
+  const T c1 = coef[2 * step], c2 = coef[2 * step + 1];
   T yx, yy;
   stencil_row<T>(st, g.plane, n, g.ld, xin, yx, yy);
   const TV bb = b[n];
   const T rx = bb.x - yx, ry = bb.y - yy;
   const T i00 = ldc<T>(dinv + n), i01 = ldc<T>(dinv + g.plane + n), i11 = ldc<T>(dinv + 2 * g.plane + n);
   const TV dold = d[n];
-  const T dx = (T)c1 * dold.x + (T)c2 * (i00 * rx + i01 * ry);
-  const T dy = (T)c1 * dold.y + (T)c2 * (i01 * rx + i11 * ry);
+  const T dx = c1 * dold.x + c2 * (i00 * rx + i01 * ry);
+  const T dy = c1 * dold.y + c2 * (i01 * rx + i11 * ry);
   d[n] = mk2<TV>(dx, dy);
   const TV xo = xin[n];
   xout[n] = mk2<TV>(xo.x + dx, xo.y + dy);
@@ -471,18 +475,27 @@ void launch_max_final(cudaStream_t s, const double* partial, int n, double* out)
   k_max_final<<<1, 1024, 0, s>>>(partial, n, out);
 }
 
-template <typename TS, typename TD, typename TV>
-void launch_cheb_zero_start(cudaStream_t s, const Layout& g, const TD* dinv, const double* lmax, double lo,
-                            const TV* b, TV* x, TV* d) {
+template <typename T>
+void launch_cheb_coefs(cudaStream_t s, const double* lmax, double lo, int deg, T* coef) {
   note_launch();
-  k_cheb_zero_start<TD, TV><<<ngrid(g), kBlk, 0, s>>>(g, dinv, lmax, lo, b, x, d);
+  k_cheb_coefs<T><<<1, 32, 0, s>>>(lmax, lo, deg, coef);
+}
+template void launch_cheb_coefs<double>(cudaStream_t, const double*, double, int, double*);
+template void launch_cheb_coefs<float>(cudaStream_t, const double*, double, int, float*);
+
+template <typename TS, typename TD, typename TV>
+void launch_cheb_zero_start(cudaStream_t s, const Layout& g, const TD* dinv,
+                            const typename ScalarOf<TV>::type* coef, const TV* b, TV* x, TV* d) {
+  note_launch();
+  k_cheb_zero_start<TD, TV><<<ngrid(g), kBlk, 0, s>>>(g, dinv, coef, b, x, d);
 }
 
 template <typename TS, typename TD, typename TV>
-void launch_cheb_sweep(cudaStream_t s, const Layout& g, const TS* st, const TD* dinv, const double* lmax, double lo,
-                       int step, const TV* xin, TV* xout, TV* d, const TV* b) {
+void launch_cheb_sweep(cudaStream_t s, const Layout& g, const TS* st, const TD* dinv,
+                       const typename ScalarOf<TV>::type* coef, int step, const TV* xin, TV* xout, TV* d,
+                       const TV* b) {
   note_launch();
-  k_cheb_sweep<TS, TD, TV><<<ngrid(g), kBlk, 0, s>>>(g, st, dinv, lmax, lo, step, xin, xout, d, b);
+  k_cheb_sweep<TS, TD, TV><<<ngrid(g), kBlk, 0, s>>>(g, st, dinv, coef, step, xin, xout, d, b);
 }
 
 template <typename TV>
@@ -537,10 +550,11 @@ void launch_convert_stencil(cudaStream_t s, const Layout& g, const TA* a, TB* b)
   template void launch_residual_stencil<TS, TV>(cudaStream_t, const Layout&, const TS*, const TV*, const TV*,    \
                                                 TV*);                                                            \
   template int launch_dinv_gershgorin<TS, TD>(cudaStream_t, const Layout&, const TS*, TD*, double*);             \
-  template void launch_cheb_zero_start<TS, TD, TV>(cudaStream_t, const Layout&, const TD*, const double*, double, \
-                                                   const TV*, TV*, TV*);                                         \
-  template void launch_cheb_sweep<TS, TD, TV>(cudaStream_t, const Layout&, const TS*, const TD*, const double*,   \
-                                              double, int, const TV*, TV*, TV*, const TV*);                      \
+  template void launch_cheb_zero_start<TS, TD, TV>(cudaStream_t, const Layout&, const TD*,                      \
+                                                   const typename ScalarOf<TV>::type*, const TV*, TV*, TV*);     \
+  template void launch_cheb_sweep<TS, TD, TV>(cudaStream_t, const Layout&, const TS*, const TD*,                 \
+                                              const typename ScalarOf<TV>::type*, int, const TV*, TV*, TV*,      \
+                                              const TV*);                                                        \
   template void launch_coarse_dense<TS>(cudaStream_t, const Layout&, const TS*, double*);
 
 SVN_INST_LEVEL(double, double, double2)

@@ -31,6 +31,7 @@ struct Level {
   __nv_bfloat16* st16 = nullptr; // mixed: BF16 copy used by the V-cycle
   void* dinv = nullptr;          // 3 planes (double or float)
   double* lmax = nullptr;        // device scalar: Gershgorin bound of D^-1 A
+  void* cheb = nullptr;          // Chebyshev step coefficients (V-cycle scalar type)
   void* x[2] = {nullptr, nullptr};
   void* d = nullptr;
   void* b = nullptr;
@@ -70,7 +71,7 @@ struct svn_handle {
   // Krylov
   int restart = 30;
   double2* V = nullptr;
-  void* Z = nullptr;            // restart vectors in the V-cycle precision
+  double2* Z = nullptr;         // preconditioned basis (FP64)
   double2* w = nullptr;
   double* hbuf = nullptr;       // device: h1 [restart+1], h2 [restart+1], nrm2
   double* ybuf = nullptr;       // device: FGMRES coefficients
@@ -79,6 +80,10 @@ struct svn_handle {
   double* scal = nullptr;       // device scalars
   double* hostbuf = nullptr;    // pinned host mirror
   size_t hostbuf_len = 0;
+
+  // the V-cycle as a CUDA graph: input in lv[0].b, output in lv[0].x[1]
+  cudaGraph_t vc_graph = nullptr;
+  cudaGraphExec_t vc_exec = nullptr;
 
   // instrumentation
   struct ProfRec {
@@ -281,6 +286,10 @@ int linearize(svn_handle* h, const double2* v, const double* pi) {
       nb = launch_dinv_gershgorin<double, double>(s, lv.g, lv.st64, (double*)lv.dinv, h->partial);
     }
     launch_max_final(s, h->partial, nb, lv.lmax);
+    if (h->mixed)
+      launch_cheb_coefs<float>(s, lv.lmax, h->prm.cheb_lo, h->prm.cheb_degree, (float*)lv.cheb);
+    else
+      launch_cheb_coefs<double>(s, lv.lmax, h->prm.cheb_lo, h->prm.cheb_degree, (double*)lv.cheb);
   }
   CKL();
   Level& lc = h->lv[L - 1];
@@ -311,15 +320,16 @@ void vcycle(svn_handle* h, int l, const TV* b, TV* xout) {
   TV* x1 = (TV*)lv.x[1];
   TV* d = (TV*)lv.d;
   TV* r = (TV*)lv.r;
+  using T = typename ScalarOf<TV>::type;
   const int deg = h->prm.cheb_degree;
-  const double lo = h->prm.cheb_lo;
+  const T* coef = (const T*)lv.cheb;
   // pre-smoothing from x = 0
-  launch_cheb_zero_start<TS, TD, TV>(s, lv.g, dinv, lv.lmax, lo, b, x0, d);
+  launch_cheb_zero_start<TS, TD, TV>(s, lv.g, dinv, coef, b, x0, d);
   TV* cur = x0;
   TV* nxt = x1;
   for (int k = 1; k < deg; ++k) {
     Prof pr(h, SVN_K_CHEB);
-    launch_cheb_sweep<TS, TD, TV>(s, lv.g, st, dinv, lv.lmax, lo, k, cur, nxt, d, b);
+    launch_cheb_sweep<TS, TD, TV>(s, lv.g, st, dinv, coef, k, cur, nxt, d, b);
     std::swap(cur, nxt);
   }
   // coarse-grid correction
@@ -332,38 +342,63 @@ void vcycle(svn_handle* h, int l, const TV* b, TV* xout) {
   for (int k = 0; k < deg; ++k) {
     TV* dst = (k == deg - 1 && xout != cur) ? xout : (cur == x0 ? x1 : x0);
     Prof pr(h, SVN_K_CHEB);
-    launch_cheb_sweep<TS, TD, TV>(s, lv.g, st, dinv, lv.lmax, lo, k, cur, dst, d, b);
+    launch_cheb_sweep<TS, TD, TV>(s, lv.g, st, dinv, coef, k, cur, dst, d, b);
     cur = dst;
   }
   if (cur != xout) cudaMemcpyAsync(xout, cur, sizeof(TV) * lv.g.plane, cudaMemcpyDeviceToDevice, s);
   (void)nxt;
 }
 
-// z = M^-1 r for a level-0 FP64 vector r; z in the V-cycle precision.
-int precondition(svn_handle* h, const double2* r, void* z) {
+// Record the V-cycle launches from lv[0].b to lv[0].x[1] on the handle's stream.
+void vcycle_record(svn_handle* h) {
   Level& l0 = h->lv[0];
+  if (h->mixed)
+    vcycle<__nv_bfloat16, float, float2>(h, 0, (const float2*)l0.b, (float2*)l0.x[1]);
+  else
+    vcycle<double, double, double2>(h, 0, (const double2*)l0.b, (double2*)l0.x[1]);
+}
+
+// z = M^-1 r for level-0 FP64 vectors r, z (one V-cycle).
+int precondition(svn_handle* h, const double2* r, double2* z) {
+  Level& l0 = h->lv[0];
+  cudaStream_t s = h->stream;
+  if (h->mixed)
+    launch_cast_d2f(s, l0.g, r, (float2*)l0.b);
+  else
+    CK(cudaMemcpyAsync(l0.b, r, sizeof(double2) * l0.g.plane, cudaMemcpyDeviceToDevice, s));
+  CKL();
   Prof pr(h, SVN_K_VCYCLE);
-  if (h->mixed) {
-    launch_cast_d2f(h->stream, l0.g, r, (float2*)l0.b);
-    vcycle<__nv_bfloat16, float, float2>(h, 0, (const float2*)l0.b, (float2*)z);
+  if (h->prm.use_graphs) {
+    if (!h->vc_exec) {
+      const bool prof = h->prof_on;
+      h->prof_on = false;   // no event records inside the capture
+      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+      vcycle_record(h);
+      cudaError_t e = cudaStreamEndCapture(s, &h->vc_graph);
+      h->prof_on = prof;
+      if (e != cudaSuccess) return fail(h, SVN_ERR_CUDA, "V-cycle capture: %s", cudaGetErrorString(e));
+      CK(cudaGraphInstantiate(&h->vc_exec, h->vc_graph, 0));
+    }
+    CK(cudaGraphLaunch(h->vc_exec, s));
   } else {
-    vcycle<double, double, double2>(h, 0, r, (double2*)z);
+    vcycle_record(h);
   }
+  CKL();
+  if (h->mixed)
+    launch_cast_f2d(s, l0.g, (const float2*)l0.x[1], z);
+  else
+    CK(cudaMemcpyAsync(z, l0.x[1], sizeof(double2) * l0.g.plane, cudaMemcpyDeviceToDevice, s));
   CKL();
   return SVN_OK;
 }
 
-// y = K0 z (FP64 outer operator), z in the V-cycle precision.
-void apply_outer(svn_handle* h, const void* z, double2* y) {
+// y = K0 z (FP64 outer operator).
+void apply_outer(svn_handle* h, const double2* z, double2* y) {
   Prof pr(h, SVN_K_APPLY);
-  if (h->mixed)
-    launch_apply<double, float2, double2, double>(h->stream, h->g0, h->lv[0].st64, (const float2*)z, y);
-  else
-    launch_apply<double, double2, double2, double>(h->stream, h->g0, h->lv[0].st64, (const double2*)z, y);
+  launch_apply<double, double2, double2, double>(h->stream, h->g0, h->lv[0].st64, z, y);
 }
 
-size_t zbytes(const svn_handle* h) { return (h->mixed ? sizeof(float2) : sizeof(double2)) * h->g0.plane; }
-void* zvec(svn_handle* h, int j) { return (char*)h->Z + (size_t)j * zbytes(h); }
+double2* zvec(svn_handle* h, int j) { return h->Z + (size_t)j * h->g0.plane; }
 
 int norm2(svn_handle* h, const double2* x, double* out) {
   launch_norm2_partial(h->stream, h->g0, x, h->partial);
@@ -402,10 +437,12 @@ int fgmres(svn_handle* h, const double2* b, double2* x, double rtol, int maxit, 
       double2* Vj = h->V + (size_t)j * vs;
       TRY(precondition(h, Vj, zvec(h, j)));
       apply_outer(h, zvec(h, j), h->w);
-      // classical Gram-Schmidt, twice
+      // classical Gram-Schmidt; a second pass only when the first one cancelled
+      // more than half of |w|^2 (Kahan's "twice is enough" criterion)
       double* h1 = h->hbuf;
       double* h2 = h->hbuf + (m + 1);
       double* nr = h->hbuf + 2 * (m + 1);
+      std::vector<double> hh(2 * (m + 1) + 1, 0.0);
       for (int pass = 0; pass < 2; ++pass) {
         double* hp = pass == 0 ? h1 : h2;
         {
@@ -413,13 +450,21 @@ int fgmres(svn_handle* h, const double2* b, double2* x, double rtol, int maxit, 
           launch_multidot(s, g, h->V, vs, j + 1, h->w, h->partial, nw);
         }
         launch_multidot_final(s, h->partial, nw, j + 1, hp, 0);
-        Prof pr(h, SVN_K_UPDATE);
-        launch_update_norm(s, g, h->V, vs, j + 1, hp, h->w, h->partial, nw);
+        {
+          Prof pr(h, SVN_K_UPDATE);
+          launch_update_norm(s, g, h->V, vs, j + 1, hp, h->w, h->partial, nw);
+        }
+        launch_sum_final(s, h->partial, nw, nr);
+        CKL();
+        TRY(sync_read(h, h->hbuf, hh.size(), hh.data()));
+        if (pass == 0) {
+          for (int i = 0; i <= j; ++i) hh[m + 1 + i] = 0.0;
+          double proj = 0.0;
+          for (int i = 0; i <= j; ++i) proj += hh[i] * hh[i];
+          const double after = hh[2 * (m + 1)];
+          if (!h->prm.reorth_always && after >= 0.5 * (proj + after)) break;
+        }
       }
-      launch_sum_final(s, h->partial, nw, nr);
-      CKL();
-      std::vector<double> hh(2 * (m + 1) + 1);
-      TRY(sync_read(h, h->hbuf, hh.size(), hh.data()));
       for (int i = 0; i <= j; ++i) H[(size_t)i * m + j] = hh[i] + hh[m + 1 + i];
       const double hn = std::sqrt(hh[2 * (m + 1)]);
       if (!std::isfinite(hn)) return fail(h, SVN_ERR_NONFINITE, "FGMRES: non-finite Arnoldi vector");
@@ -454,10 +499,7 @@ int fgmres(svn_handle* h, const double2* b, double2* x, double rtol, int maxit, 
     }
     memcpy(h->hostbuf, yv.data(), sizeof(double) * jdone);
     CK(cudaMemcpyAsync(h->ybuf, h->hostbuf, sizeof(double) * jdone, cudaMemcpyHostToDevice, s));
-    if (h->mixed)
-      launch_lincomb<float2>(s, g, (const float2*)h->Z, vs, jdone, h->ybuf, x);
-    else
-      launch_lincomb<double2>(s, g, (const double2*)h->Z, vs, jdone, h->ybuf, x);
+    launch_lincomb<double2>(s, g, h->Z, vs, jdone, h->ybuf, x);
     CKL();
     CK(cudaStreamSynchronize(s));   // hostbuf reuse
     const double est = std::fabs(gv[jdone]);
@@ -539,6 +581,7 @@ int create_impl(svn_handle* h, const svn_grid* g, const svn_params* p, void* str
     if (h->mixed) TRY(dalloc(h, &L.st16, (size_t)NSTEN * lp));
     TRY(dalloc(h, (char**)&L.dinv, 3 * lp * (h->mixed ? sizeof(float) : sizeof(double))));
     TRY(dalloc(h, &L.lmax, 1));
+    TRY(dalloc(h, (double**)&L.cheb, 2 * (size_t)p->cheb_degree));
     for (int k = 0; k < 2; ++k) TRY(dalloc(h, (char**)&L.x[k], lp * vsz));
     TRY(dalloc(h, (char**)&L.d, lp * vsz));
     TRY(dalloc(h, (char**)&L.b, lp * vsz));
@@ -550,7 +593,7 @@ int create_impl(svn_handle* h, const svn_grid* g, const svn_params* p, void* str
   TRY(dalloc(h, &h->dense_inv, (size_t)h->ncoarse * h->ncoarse));
   TRY(dalloc(h, &h->info, 4));
   TRY(dalloc(h, &h->V, (size_t)(h->restart + 1) * pl));
-  TRY(dalloc(h, (char**)&h->Z, (size_t)h->restart * pl * vsz));
+  TRY(dalloc(h, &h->Z, (size_t)h->restart * pl));
   TRY(dalloc(h, &h->hbuf, 2 * (size_t)(h->restart + 1) + 1));
   TRY(dalloc(h, &h->ybuf, (size_t)h->restart + 1));
   const int nw = krylov_blocks(g0);
@@ -570,10 +613,14 @@ void destroy_impl(svn_handle* h) {
   dfree(h->v); dfree(h->dv); dfree(h->vt); dfree(h->R); dfree(h->rhs); dfree(h->w);
   dfree(h->pi); dfree(h->pi_scratch); dfree(h->eb);
   for (Level& L : h->lv) {
-    dfree(L.st64); dfree(L.st16); dfree(L.dinv); dfree(L.lmax);
+    dfree(L.st64); dfree(L.st16); dfree(L.dinv); dfree(L.lmax); dfree(L.cheb);
     dfree(L.x[0]); dfree(L.x[1]); dfree(L.d); dfree(L.b); dfree(L.r);
   }
   dfree(h->dense); dfree(h->dense_inv); dfree(h->info);
+  if (h->vc_exec) cudaGraphExecDestroy(h->vc_exec);
+  if (h->vc_graph) cudaGraphDestroy(h->vc_graph);
+  h->vc_exec = nullptr;
+  h->vc_graph = nullptr;
   dfree(h->V); dfree(h->Z); dfree(h->hbuf); dfree(h->ybuf); dfree(h->partial); dfree(h->scal);
   if (h->hostbuf) cudaFreeHost(h->hostbuf);
   h->hostbuf = nullptr;
@@ -646,6 +693,7 @@ int step_impl(svn_handle* h, double dt, double tol, svn_stats* st) {
     TRY(energy(h, h->v, h->v, &a0, 1, &phi0, &scale0));
   }
   const svn_params& p = h->prm;
+  double eta_prev = p.ew_eta_max;
   for (int it = 0;; ++it) {
     double r;
     TRY(residual(h, h->v, h->R, &r));
@@ -663,12 +711,19 @@ int step_impl(svn_handle* h, double dt, double tol, svn_stats* st) {
     CKL();
     int kits = 0;
     double eta = p.krylov_rtol;
-    if (p.eisenstat_walker && it > 0) {
-      // Eisenstat-Walker choice 2: eta = 0.9 (r / r_prev)^2, safeguarded
-      const double ratio = r / st->res_hist[it - 1];
-      eta = std::min(0.5, std::max(p.krylov_rtol, 0.9 * ratio * ratio));
-    } else if (p.eisenstat_walker) {
-      eta = 0.5;
+    if (p.eisenstat_walker) {
+      // Eisenstat-Walker choice 2: eta_k = 0.9 (r_k / r_{k-1})^2 with the
+      // safeguard eta_k >= 0.9 eta_{k-1}^2 when that is above 0.1, clipped
+      // to [krylov_rtol, ew_eta_max]
+      eta = p.ew_eta_max;
+      if (it > 0) {
+        const double ratio = r / st->res_hist[it - 1];
+        eta = 0.9 * ratio * ratio;
+        const double prev = 0.9 * eta_prev * eta_prev;
+        if (prev > 0.1) eta = std::max(eta, prev);
+        eta = std::min(p.ew_eta_max, std::max(p.krylov_rtol, eta));
+      }
+      eta_prev = eta;
     }
     TRY(fgmres(h, h->rhs, h->dv, eta, p.max_krylov, &kits));
     st->krylov_per_newton[it] = kits;
@@ -731,10 +786,13 @@ int svn_default_params(svn_params* p) {
   p->max_krylov = 600;
   p->precision = SVN_FP64;
   p->cheb_degree = 3;
-  p->cheb_lo = 0.1;
-  p->coarse_N = 8;
+  p->cheb_lo = 0.05;
+  p->coarse_N = 4;
   p->eisenstat_walker = 0;
   p->learned = 0;
+  p->use_graphs = 1;
+  p->reorth_always = 0;
+  p->ew_eta_max = 0.1;
   return SVN_OK;
 }
 
@@ -875,9 +933,7 @@ int svn_precondition(svn_handle* h, const double* r, double* z) {
   const Layout& g = h->g0;
   launch_unpack_nodes(h->stream, g, r, h->vt);
   CKL();
-  TRY(precondition(h, h->vt, h->Z));
-  if (h->mixed) launch_cast_f2d(h->stream, g, (const float2*)h->Z, h->w);
-  else CK(cudaMemcpyAsync(h->w, h->Z, sizeof(double2) * g.plane, cudaMemcpyDeviceToDevice, h->stream));
+  TRY(precondition(h, h->vt, h->w));
   launch_pack_nodes(h->stream, g, h->w, z);
   CKL();
   CK(cudaStreamSynchronize(h->stream));

@@ -148,6 +148,10 @@ template <> __device__ __forceinline__ __nv_bfloat16 from_d<__nv_bfloat16>(doubl
 template <typename T> __device__ __forceinline__ double to_d(T x) { return (double)x; }
 template <> __device__ __forceinline__ double to_d<__nv_bfloat16>(__nv_bfloat16 x) { return (double)__bfloat162float(x); }
 
+template <typename V> struct ScalarOf;
+template <> struct ScalarOf<double2> { using type = double; };
+template <> struct ScalarOf<float2> { using type = float; };
+
 template <typename T> struct Vec2;
 template <> struct Vec2<double> { using type = double2; };
 template <> struct Vec2<float> { using type = float2; };
