@@ -91,6 +91,9 @@ typedef struct svn_params {
   int reorth_always;        /* 1: always two Gram-Schmidt passes; 0: second pass only
                                when the first cancels more than half of |w|^2 */
   double ew_eta_max;        /* upper bound of the Eisenstat-Walker forcing term */
+  int lmax_iters;           /* power-method steps for lambda_max(D^-1 A) per level
+                               (0: Gershgorin bound) */
+  double lmax_safety;       /* the estimate is multiplied by this factor */
 } svn_params;
 
 typedef struct svn_stats {

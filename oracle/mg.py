@@ -86,6 +86,25 @@ def gershgorin_lmax(A, Dinv):
     return float(np.asarray(M.sum(axis=1)).max())
 
 
+def checkerboard(N):
+    """Deterministic start vector on the interior nodes of the N-cell grid:
+    x[i, j] = ((-1)^(i+j), -(-1)^(i+j)) (high-frequency in both components)."""
+    jj, ii = np.meshgrid(np.arange(1, N), np.arange(1, N), indexing="ij")
+    s = (-1.0) ** (ii + jj)
+    return np.stack([s, -s], -1).reshape(-1)
+
+
+def power_lmax(A, Dinv, N, iters=15, safety=1.15):
+    """Estimate of lambda_max(D^-1 A) by ``iters`` steps of the power method
+    from the checkerboard vector: safety * |x_k| / |x_{k-1}| (no
+    normalisation between steps)."""
+    x = checkerboard(N)
+    prev = x
+    for _ in range(iters):
+        prev, x = x, Dinv @ (A @ x)
+    return safety * np.linalg.norm(x) / np.linalg.norm(prev)
+
+
 def chebyshev(A, Dinv, b, x, degree, lmax, lo=0.1):
     """``degree`` steps of Chebyshev iteration for D^-1 A on [lo lmax, lmax].
 
@@ -117,8 +136,11 @@ class Level:
     chol: object = None
 
 
-def build_hierarchy(A0, N, coarse_N=8, lo=0.1):
-    """Galerkin hierarchy N, N/2, ... down to ``coarse_N`` cells."""
+def build_hierarchy(A0, N, coarse_N=8, lo=0.1, power_iters=0, safety=1.15):
+    """Galerkin hierarchy N, N/2, ... down to ``coarse_N`` cells.
+
+    lambda_max(D^-1 A) per level: the Gershgorin bound (power_iters = 0) or
+    the power-method estimate ``power_lmax``."""
     levels = [Level(A0.tocsr())]
     n = N
     while n > coarse_N and n % 2 == 0:
@@ -126,9 +148,14 @@ def build_hierarchy(A0, N, coarse_N=8, lo=0.1):
         levels[-1].P = P
         levels.append(Level(galerkin(levels[-1].A, P)))
         n //= 2
+    n = N
     for lv in levels[:-1]:
         lv.Dinv = block_diag_inverse(lv.A)
-        lv.lmax = gershgorin_lmax(lv.A, lv.Dinv)
+        if power_iters > 0:
+            lv.lmax = power_lmax(lv.A, lv.Dinv, n, power_iters, safety)
+        else:
+            lv.lmax = gershgorin_lmax(lv.A, lv.Dinv)
+        n //= 2
     levels[-1].chol = sla.cho_factor(levels[-1].A.toarray(), lower=True)
     return levels
 

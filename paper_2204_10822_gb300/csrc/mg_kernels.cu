@@ -168,6 +168,60 @@ __global__ void k_dinv_gershgorin(Layout g, const TS* __restrict__ st, TD* __res
   if (threadIdx.x == 0 && threadIdx.y == 0) partial[blockIdx.y * gridDim.x + blockIdx.x] = gmax;
 }
 
+// Start vector of the power method: ((-1)^(i+j), -(-1)^(i+j)) on interior nodes.
+template <typename TV>
+__global__ void k_checkerboard(Layout g, TV* __restrict__ x) {
+  using T = typename ScalarOf<TV>::type;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > g.N || j > g.N) return;
+  const T sgn = ((i + j) & 1) ? T(-1) : T(1);
+  x[(long long)j * g.ld + i] = is_interior(i, j, g.N) ? mk2<TV>(sgn, -sgn) : mk2<TV>(T(0), T(0));
+}
+
+// y = D^-1 (A x) on interior nodes (one power-method step).
+template <typename TS, typename TD, typename TV>
+__global__ void k_power_step(Layout g, const TS* __restrict__ st, const TD* __restrict__ dinv,
+                             const TV* __restrict__ x, TV* __restrict__ y) {
+  using T = typename ScalarOf<TV>::type;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i > g.N || j > g.N) return;
+  const long long n = (long long)j * g.ld + i;
+  TV out = mk2<TV>(T(0), T(0));
+  if (is_interior(i, j, g.N)) {
+    T ax, ay;
+    stencil_row<T>(st, g.plane, n, g.ld, x, ax, ay);
+    const T i00 = ldc<T>(dinv + n), i01 = ldc<T>(dinv + g.plane + n), i11 = ldc<T>(dinv + 2 * g.plane + n);
+    out = mk2<TV>(i00 * ax + i01 * ay, i01 * ax + i11 * ay);
+  }
+  y[n] = out;
+}
+
+template <typename TV>
+__global__ void k_norm2_vec(long long n, const TV* __restrict__ x, double* __restrict__ partial) {
+  double s = 0.0;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const TV v = x[t];
+    s += (double)v.x * (double)v.x + (double)v.y * (double)v.y;
+  }
+  s = block_sum(s);
+  if (threadIdx.x == 0) partial[blockIdx.x] = s;
+}
+
+// lmax = safety * sqrt(sum(p_last) / sum(p_prev)) over nb block partials each.
+__global__ void k_lmax_from_norms(const double* __restrict__ p_last, const double* __restrict__ p_prev, int nb,
+                                  double safety, double* __restrict__ lmax) {
+  double a = 0.0, b = 0.0;
+  for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+    a += p_last[t];
+    b += p_prev[t];
+  }
+  a = block_sum(a);
+  b = block_sum(b);
+  if (threadIdx.x == 0) *lmax = safety * sqrt(a / b);
+}
+
 __global__ void k_max_final(const double* __restrict__ partial, int n, double* __restrict__ out) {
   double m = 0.0;
   for (int b = threadIdx.x; b < n; b += blockDim.x) m = fmax(m, partial[b]);
@@ -469,6 +523,36 @@ int launch_dinv_gershgorin(cudaStream_t s, const Layout& g, const TS* st, TD* di
   k_dinv_gershgorin<TS, TD><<<gr, kBlk, 0, s>>>(g, st, dinv, partial);
   return gr.x * gr.y;
 }
+
+template <typename TS, typename TD, typename TV>
+void launch_power_lmax(cudaStream_t s, const Layout& g, const TS* st, const TD* dinv, int iters, double safety,
+                       TV* x0, TV* x1, double* partial, double* lmax) {
+  note_launch();
+  k_checkerboard<TV><<<ngrid(g), kBlk, 0, s>>>(g, x0);
+  TV* a = x0;
+  TV* b = x1;
+  for (int k = 0; k < iters; ++k) {
+    note_launch();
+    k_power_step<TS, TD, TV><<<ngrid(g), kBlk, 0, s>>>(g, st, dinv, a, b);
+    TV* t = a;
+    a = b;
+    b = t;
+  }
+  // a = x_iters, b = x_{iters-1}
+  long long nb = (g.plane + 255) / 256;
+  if (nb > 1024) nb = 1024;
+  note_launch();
+  k_norm2_vec<TV><<<(unsigned)nb, 256, 0, s>>>(g.plane, a, partial);
+  note_launch();
+  k_norm2_vec<TV><<<(unsigned)nb, 256, 0, s>>>(g.plane, b, partial + nb);
+  note_launch();
+  k_lmax_from_norms<<<1, 1024, 0, s>>>(partial, partial + nb, (int)nb, safety, lmax);
+}
+template void launch_power_lmax<double, double, double2>(cudaStream_t, const Layout&, const double*, const double*,
+                                                         int, double, double2*, double2*, double*, double*);
+template void launch_power_lmax<__nv_bfloat16, float, float2>(cudaStream_t, const Layout&, const __nv_bfloat16*,
+                                                              const float*, int, double, float2*, float2*, double*,
+                                                              double*);
 
 void launch_max_final(cudaStream_t s, const double* partial, int n, double* out) {
   note_launch();

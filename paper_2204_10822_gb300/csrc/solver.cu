@@ -84,6 +84,7 @@ struct svn_handle {
   // the V-cycle as a CUDA graph: input in lv[0].b, output in lv[0].x[1]
   cudaGraph_t vc_graph = nullptr;
   cudaGraphExec_t vc_exec = nullptr;
+  cudaStream_t cap_stream = nullptr;   // private stream used only to record the graph
 
   // instrumentation
   struct ProfRec {
@@ -286,6 +287,16 @@ int linearize(svn_handle* h, const double2* v, const double* pi) {
       nb = launch_dinv_gershgorin<double, double>(s, lv.g, lv.st64, (double*)lv.dinv, h->partial);
     }
     launch_max_final(s, h->partial, nb, lv.lmax);
+    if (h->prm.lmax_iters > 0) {
+      if (h->mixed)
+        launch_power_lmax<__nv_bfloat16, float, float2>(s, lv.g, lv.st16, (const float*)lv.dinv, h->prm.lmax_iters,
+                                                        h->prm.lmax_safety, (float2*)lv.x[0], (float2*)lv.x[1],
+                                                        h->partial, lv.lmax);
+      else
+        launch_power_lmax<double, double, double2>(s, lv.g, lv.st64, (const double*)lv.dinv, h->prm.lmax_iters,
+                                                   h->prm.lmax_safety, (double2*)lv.x[0], (double2*)lv.x[1],
+                                                   h->partial, lv.lmax);
+    }
     if (h->mixed)
       launch_cheb_coefs<float>(s, lv.lmax, h->prm.cheb_lo, h->prm.cheb_degree, (float*)lv.cheb);
     else
@@ -370,11 +381,18 @@ int precondition(svn_handle* h, const double2* r, double2* z) {
   Prof pr(h, SVN_K_VCYCLE);
   if (h->prm.use_graphs) {
     if (!h->vc_exec) {
+      // record on a private stream (the caller's stream may be the legacy
+      // default stream, which cannot be captured); launch on the caller's
+      if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
       const bool prof = h->prof_on;
       h->prof_on = false;   // no event records inside the capture
-      CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-      vcycle_record(h);
-      cudaError_t e = cudaStreamEndCapture(s, &h->vc_graph);
+      h->stream = h->cap_stream;
+      cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        vcycle_record(h);
+        e = cudaStreamEndCapture(h->cap_stream, &h->vc_graph);
+      }
+      h->stream = s;
       h->prof_on = prof;
       if (e != cudaSuccess) return fail(h, SVN_ERR_CUDA, "V-cycle capture: %s", cudaGetErrorString(e));
       CK(cudaGraphInstantiate(&h->vc_exec, h->vc_graph, 0));
@@ -528,6 +546,8 @@ int check_params(svn_handle* h, const svn_params* p) {
   if (!(p->cheb_lo > 0.0 && p->cheb_lo < 1.0)) return fail(h, SVN_ERR_ARG, "cheb_lo must be in (0, 1)");
   if (p->precision != SVN_FP64 && p->precision != SVN_MIXED) return fail(h, SVN_ERR_ARG, "unknown precision");
   if (p->coarse_N < 2 || p->coarse_N > 16) return fail(h, SVN_ERR_ARG, "coarse_N must be in [2, 16]");
+  if (p->lmax_iters < 0 || p->lmax_iters > 60) return fail(h, SVN_ERR_ARG, "lmax_iters must be in [0, 60]");
+  if (!(p->lmax_safety >= 1.0 && p->lmax_safety < 4.0)) return fail(h, SVN_ERR_ARG, "lmax_safety must be in [1, 4)");
   return SVN_OK;
 }
 
@@ -621,6 +641,8 @@ void destroy_impl(svn_handle* h) {
   if (h->vc_graph) cudaGraphDestroy(h->vc_graph);
   h->vc_exec = nullptr;
   h->vc_graph = nullptr;
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  h->cap_stream = nullptr;
   dfree(h->V); dfree(h->Z); dfree(h->hbuf); dfree(h->ybuf); dfree(h->partial); dfree(h->scal);
   if (h->hostbuf) cudaFreeHost(h->hostbuf);
   h->hostbuf = nullptr;
@@ -793,6 +815,8 @@ int svn_default_params(svn_params* p) {
   p->use_graphs = 1;
   p->reorth_always = 0;
   p->ew_eta_max = 0.1;
+  p->lmax_iters = 15;
+  p->lmax_safety = 1.15;
   return SVN_OK;
 }
 

@@ -142,22 +142,23 @@ def test_vcycle_parity_fp64():
     N = 64
     p = W.make_problem(N, seed=5)
     st = Step(p)
-    s = make_solver(p, coarse_N=8, cheb_degree=3, cheb_lo=0.1)
-    v = rand_v(N, 5)
-    pi = st.pi_of(v)
-    s.linearize(p.dt, dev(v), dev(pi))
-    levels = mg.build_hierarchy(st.svn_matrix(v, pi), N, coarse_N=8)
-    r = rand_v(N, 6, 1.0)
-    z = host(s.precondition(dev(r)))
-    zo = st.from_free(mg.vcycle(levels, st.to_free(r), degree=3, lo=0.1))
-    assert relmax(z, zo) < 1e-9
+    for iters in (0, 15):       # Gershgorin bound, power-method estimate
+        s = make_solver(p, coarse_N=8, cheb_degree=3, cheb_lo=0.1, lmax_iters=iters)
+        v = rand_v(N, 5)
+        pi = st.pi_of(v)
+        s.linearize(p.dt, dev(v), dev(pi))
+        levels = mg.build_hierarchy(st.svn_matrix(v, pi), N, coarse_N=8, power_iters=iters)
+        r = rand_v(N, 6, 1.0)
+        z = host(s.precondition(dev(r)))
+        zo = st.from_free(mg.vcycle(levels, st.to_free(r), degree=3, lo=0.1))
+        assert relmax(z, zo) < 1e-9, iters
 
 
 def test_krylov_solve_parity():
     N = 64
     p = W.make_problem(N, seed=6)
     st = Step(p)
-    s = make_solver(p, coarse_N=8)
+    s = make_solver(p, coarse_N=8, cheb_degree=3, cheb_lo=0.05)
     v = rand_v(N, 6)
     pi = st.pi_of(v)
     s.linearize(p.dt, dev(v), dev(pi))
@@ -166,8 +167,8 @@ def test_krylov_solve_parity():
     x, its = s.krylov_solve(dev(b), 1e-8)
     xf, bf = st.to_free(host(x)), st.to_free(b)
     assert np.linalg.norm(bf - K @ xf) <= 1.05e-8 * np.linalg.norm(bf)
-    levels = mg.build_hierarchy(K, N, coarse_N=8)
-    _, its_o, _ = mg.fgmres(K, bf, M=lambda r: mg.vcycle(levels, r), rtol=1e-8, restart=30)
+    levels = mg.build_hierarchy(K, N, coarse_N=8, power_iters=15)
+    _, its_o, _ = mg.fgmres(K, bf, M=lambda r: mg.vcycle(levels, r, degree=3, lo=0.05), rtol=1e-8, restart=30)
     assert abs(its - its_o) <= 1, (its, its_o)
 
 

@@ -133,3 +133,14 @@ def test_fgmres_textbook_properties():
     xe = lu.solve(b)
     assert np.linalg.norm(b - K @ x) <= 1.01e-9 * np.linalg.norm(b)
     assert it > 20          # went through at least one restart
+
+
+
+def test_power_lmax_converges_to_eigs():
+    import scipy.sparse.linalg as spla2
+    st, K = svn_operator(N=16)
+    Dinv = mg.block_diag_inverse(K)
+    true = spla2.eigs((Dinv @ K).tocsr(), k=1, which="LR", return_eigenvectors=False, tol=1e-10).real.max()
+    assert abs(mg.power_lmax(K, Dinv, 16, iters=100, safety=1.0) / true - 1) < 1e-3
+    est = mg.power_lmax(K, Dinv, 16, iters=15, safety=1.0)
+    assert 0.8 * true <= est <= 1.01 * true
