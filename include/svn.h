@@ -94,6 +94,8 @@ typedef struct svn_params {
   int lmax_iters;           /* power-method steps for lambda_max(D^-1 A) per level
                                (0: Gershgorin bound) */
   double lmax_safety;       /* the estimate is multiplied by this factor */
+  int vcycle_fp32;          /* mixed precision: 1 stores the V-cycle stencils in FP32
+                               instead of BF16 */
 } svn_params;
 
 typedef struct svn_stats {

@@ -31,7 +31,8 @@ class SvnParams(ctypes.Structure):
         ("krylov_rtol", c_double), ("restart", c_int), ("max_krylov", c_int), ("precision", c_int),
         ("cheb_degree", c_int), ("cheb_lo", c_double), ("coarse_N", c_int), ("eisenstat_walker", c_int),
         ("learned", c_int), ("use_graphs", c_int), ("reorth_always", c_int),
-        ("ew_eta_max", c_double), ("lmax_iters", c_int), ("lmax_safety", c_double)]
+        ("ew_eta_max", c_double), ("lmax_iters", c_int), ("lmax_safety", c_double),
+        ("vcycle_fp32", c_int)]
 
 
 class SvnStats(ctypes.Structure):

@@ -550,6 +550,8 @@ void launch_power_lmax(cudaStream_t s, const Layout& g, const TS* st, const TD* 
 }
 template void launch_power_lmax<double, double, double2>(cudaStream_t, const Layout&, const double*, const double*,
                                                          int, double, double2*, double2*, double*, double*);
+template void launch_power_lmax<float, float, float2>(cudaStream_t, const Layout&, const float*, const float*, int,
+                                                       double, float2*, float2*, double*, double*);
 template void launch_power_lmax<__nv_bfloat16, float, float2>(cudaStream_t, const Layout&, const __nv_bfloat16*,
                                                               const float*, int, double, float2*, float2*, double*,
                                                               double*);

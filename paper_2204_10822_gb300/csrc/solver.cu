@@ -29,6 +29,7 @@ struct Level {
   Layout g;
   double* st64 = nullptr;        // FP64 stencil (19 planes)
   __nv_bfloat16* st16 = nullptr; // mixed: BF16 copy used by the V-cycle
+  float* st32 = nullptr;         // mixed with FP32 V-cycle storage
   void* dinv = nullptr;          // 3 planes (double or float)
   double* lmax = nullptr;        // device scalar: Gershgorin bound of D^-1 A
   void* cheb = nullptr;          // Chebyshev step coefficients (V-cycle scalar type)
@@ -281,14 +282,21 @@ int linearize(svn_handle* h, const double2* v, const double* pi) {
     Level& lv = h->lv[l];
     int nb;
     if (h->mixed) {
-      launch_convert_stencil<double, __nv_bfloat16>(s, lv.g, lv.st64, lv.st16);
+      if (h->prm.vcycle_fp32)
+        launch_convert_stencil<double, float>(s, lv.g, lv.st64, lv.st32);
+      else
+        launch_convert_stencil<double, __nv_bfloat16>(s, lv.g, lv.st64, lv.st16);
       nb = launch_dinv_gershgorin<double, float>(s, lv.g, lv.st64, (float*)lv.dinv, h->partial);
     } else {
       nb = launch_dinv_gershgorin<double, double>(s, lv.g, lv.st64, (double*)lv.dinv, h->partial);
     }
     launch_max_final(s, h->partial, nb, lv.lmax);
     if (h->prm.lmax_iters > 0) {
-      if (h->mixed)
+      if (h->mixed && h->prm.vcycle_fp32)
+        launch_power_lmax<float, float, float2>(s, lv.g, lv.st32, (const float*)lv.dinv, h->prm.lmax_iters,
+                                                h->prm.lmax_safety, (float2*)lv.x[0], (float2*)lv.x[1], h->partial,
+                                                lv.lmax);
+      else if (h->mixed)
         launch_power_lmax<__nv_bfloat16, float, float2>(s, lv.g, lv.st16, (const float*)lv.dinv, h->prm.lmax_iters,
                                                         h->prm.lmax_safety, (float2*)lv.x[0], (float2*)lv.x[1],
                                                         h->partial, lv.lmax);
@@ -325,7 +333,7 @@ void vcycle(svn_handle* h, int l, const TV* b, TV* xout) {
     launch_coarse_solve<TV>(s, lv.g, h->ncoarse, h->dense_inv, b, xout);
     return;
   }
-  const TS* st = h->mixed ? (const TS*)lv.st16 : (const TS*)lv.st64;
+  const TS* st = !h->mixed ? (const TS*)lv.st64 : h->prm.vcycle_fp32 ? (const TS*)lv.st32 : (const TS*)lv.st16;
   const TD* dinv = (const TD*)lv.dinv;
   TV* x0 = (TV*)lv.x[0];
   TV* x1 = (TV*)lv.x[1];
@@ -363,7 +371,9 @@ void vcycle(svn_handle* h, int l, const TV* b, TV* xout) {
 // Record the V-cycle launches from lv[0].b to lv[0].x[1] on the handle's stream.
 void vcycle_record(svn_handle* h) {
   Level& l0 = h->lv[0];
-  if (h->mixed)
+  if (h->mixed && h->prm.vcycle_fp32)
+    vcycle<float, float, float2>(h, 0, (const float2*)l0.b, (float2*)l0.x[1]);
+  else if (h->mixed)
     vcycle<__nv_bfloat16, float, float2>(h, 0, (const float2*)l0.b, (float2*)l0.x[1]);
   else
     vcycle<double, double, double2>(h, 0, (const double2*)l0.b, (double2*)l0.x[1]);
@@ -598,7 +608,8 @@ int create_impl(svn_handle* h, const svn_grid* g, const svn_params* p, void* str
     Level& L = h->lv[l];
     const long long lp = L.g.plane;
     TRY(dalloc(h, &L.st64, (size_t)NSTEN * lp));
-    if (h->mixed) TRY(dalloc(h, &L.st16, (size_t)NSTEN * lp));
+    if (h->mixed && !p->vcycle_fp32) TRY(dalloc(h, &L.st16, (size_t)NSTEN * lp));
+    if (h->mixed && p->vcycle_fp32) TRY(dalloc(h, &L.st32, (size_t)NSTEN * lp));
     TRY(dalloc(h, (char**)&L.dinv, 3 * lp * (h->mixed ? sizeof(float) : sizeof(double))));
     TRY(dalloc(h, &L.lmax, 1));
     TRY(dalloc(h, (double**)&L.cheb, 2 * (size_t)p->cheb_degree));
@@ -633,7 +644,7 @@ void destroy_impl(svn_handle* h) {
   dfree(h->v); dfree(h->dv); dfree(h->vt); dfree(h->R); dfree(h->rhs); dfree(h->w);
   dfree(h->pi); dfree(h->pi_scratch); dfree(h->eb);
   for (Level& L : h->lv) {
-    dfree(L.st64); dfree(L.st16); dfree(L.dinv); dfree(L.lmax); dfree(L.cheb);
+    dfree(L.st64); dfree(L.st16); dfree(L.st32); dfree(L.dinv); dfree(L.lmax); dfree(L.cheb);
     dfree(L.x[0]); dfree(L.x[1]); dfree(L.d); dfree(L.b); dfree(L.r);
   }
   dfree(h->dense); dfree(h->dense_inv); dfree(h->info);
