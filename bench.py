@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison step")
     return ap.parse_args()
 
 
@@ -121,24 +122,18 @@ class ClockSampler:
                 "reasons": reasons, "samples": len(rows)}
 
 
-# algorithmic bytes per unit (node) of each kernel class; the roofline block
-# reports the class with the largest share of the timed region
-def algorithmic(kclass: str, N: int, mixed: bool, stats: list[dict], restart: int):
-    nodes = (N + 1) ** 2
-    if kclass == "apply":
-        per_node = 16 + 16 + 19 * 8      # x f64 + y f64 + 19 f64 coefficients
-        return per_node * nodes, "hbm"
-    if kclass in ("multidot", "update"):
-        # pass reads (j+1) basis vectors + w (multidot) / + w read+write (update), j per Krylov iteration
-        tot = 0
-        for st in stats:
-            for k in st["krylov_per_newton"]:
-                for it in range(k):
-                    j = it % restart
-                    vecs = (j + 1) + (1 if kclass == "multidot" else 2)
-                    tot += 2 * vecs * 16 * nodes        # CGS2: two passes
-        return tot, "hbm"
-    return None, None
+# Solver settings of the timed workload (chosen by the parameter sweeps).
+SETTINGS = dict(eisenstat_walker=1, krylov_rtol=1e-4, ew_eta_max=0.1, max_krylov=600, cheb_degree=6,
+                cheb_lo=0.02, coarse_N=4, lmax_iters=15)
+FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2070 MHz
+
+
+def sweep_bytes_per_node(mixed: bool, fp32_coef: bool) -> int:
+    """Algorithmic bytes of one finest-level Chebyshev sweep per node:
+    19 stencil values, 3 block-Jacobi values, x (read), b, d (read + write), x (write)."""
+    if not mixed:
+        return 19 * 8 + 3 * 8 + 16 * 5
+    return 19 * (4 if fp32_coef else 2) + 3 * 4 + 8 * 5
 
 
 def run_ours(args, rank, world):
@@ -152,7 +147,8 @@ def run_ours(args, rank, world):
     torch.cuda.set_device(local)
     N = args.N
     p = W.config(2, N=N)
-    kw = dict(precision=args.precision, eisenstat_walker=1, krylov_rtol=1e-4, max_krylov=600)
+    mixed = args.precision == "mixed"
+    kw = dict(SETTINGS, precision=args.precision, vcycle_fp32=1 if mixed else 0)
     s = Solver(N, p.L, **kw)
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
     dev_in = [t(p.h), t(p.A), t(p.wind), t(p.ocean), t(p.v_old)]
@@ -214,28 +210,52 @@ def run_ours(args, rank, world):
                "h2d_bytes_per_step": int(sum(x.numel() * 8 for x in host_in)),
                "d2h_bytes_per_step": int(host_out.numel() * 8)}
 
+    # the plain FP64 path on the same workload, for the mixed-vs-FP64 comparison
+    fp64 = None
+    if mixed and not args.no_fp64:
+        s64 = Solver(N, p.L, **dict(SETTINGS, precision="fp64"))
+        s64.set_forcing(*dev_in)
+        s64.step(p.dt, args.tol, out=out)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        _, st64 = s64.step(p.dt, args.tol, out=out)
+        f1.record()
+        torch.cuda.synchronize()
+        fp64 = {"s_per_step": f0.elapsed_time(f1) / 1000.0, "newton_iters": st64["newton_iters"],
+                "krylov_iters": st64["krylov_iters_total"]}
+        s64.close()
+
     result = None
     if rank == 0:
         dom = max(("apply", "cheb", "multidot", "update", "element", "residual", "energy", "dual", "rap"),
                   key=lambda k: prof[k][0])
-        roof = None
         peaks = {}
         pk_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
         if os.path.exists(pk_path):
             peaks = json.load(open(pk_path))
         hbm_peak = peaks.get("hbm_gbs", 6800.0)
-        peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
-        # the headline roofline: the FP64 outer Jacobian apply (the operator of every Krylov iteration)
-        for kc in ("apply",):
-            ms, n = prof[kc]
-            byt, bound = algorithmic(kc, N, args.precision == "mixed", stats, s.params.restart)
-            if n and byt:
-                avg_s = ms / 1000.0 / n
-                ach = byt / avg_s / 1e9
-                roof = {"kernel": "k_apply (FP64 stencil Jacobian apply)", "bound": bound, "achieved": ach,
-                        "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s", "frac": ach / hbm_peak,
-                        "traffic": None, "launches": n, "avg_us": avg_s * 1e6,
-                        "algorithmic_bytes_per_launch": byt}
+        peak_src = "of measured" if "hbm_gbs" in peaks else "of fallback"
+        nodes = (N + 1) ** 2
+        roof = None
+        ms, n = prof["cheb"]
+        if n:
+            byt = sweep_bytes_per_node(mixed, True) * nodes
+            avg_s = ms / 1000.0 / n
+            ach = byt / avg_s / 1e9
+            roof = {"kernel": "k_cheb_sweep (finest-level Chebyshev-Jacobi sweep, %s)" % (
+                        "FP32 stencil, FP32 vectors" if mixed else "FP64"),
+                    "bound": "hbm", "achieved": ach, "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
+                    "frac": ach / hbm_peak, "traffic": None, "launches": n, "avg_us": avg_s * 1e6,
+                    "algorithmic_bytes_per_launch": byt}
+        roof64 = None
+        ms, n = prof["apply"]
+        if n:
+            avg_s = ms / 1000.0 / n
+            ach = 72.0 * nodes / avg_s / 1e12
+            roof64 = {"kernel": "k_apply (FP64 outer Jacobian apply, 36 DFMA per node)", "bound": "alu",
+                      "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
+                      "avg_us": avg_s * 1e6, "launches": n, "hbm_gbs": 184.0 * nodes / avg_s / 1e9}
         shares = {k: round(prof[k][0] / 1000.0 / elapsed, 4) for k in prof}
         result = {
             "metric": METRIC, "value": tmax / (args.steps * world), "unit": UNIT, "n_gpus": world,
@@ -248,8 +268,9 @@ def run_ours(args, rank, world):
             "rel_res_final": [st["rel_res_final"] for st in stats],
             "krylov_per_newton": stats[0]["krylov_per_newton"],
             "alpha_hist": stats[0]["alpha_hist"],
-            "gpu_launches": int(launches), "clocks": clk, "roofline": roof,
-            "kernel_share": shares, "dominant_kernel_class": dom, "e2e": e2e,
+            "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "roofline_fp64_apply": roof64,
+            "kernel_share": shares, "dominant_kernel_class": dom, "e2e": e2e, "fp64_path": fp64,
+            "speedup_vs_fp64": (fp64["s_per_step"] / (tmax / args.steps)) if fp64 else None,
         }
     return result
 

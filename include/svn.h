@@ -190,7 +190,7 @@ int svn_dual_update(svn_handle* h, double dt, const double* v, const double* dv,
  * one kernel class on the handle's stream, for roofline reporting. ---- */
 enum svn_kernel_class {
   SVN_K_APPLY = 0,     /* FP64 outer Jacobian apply (stencil form) */
-  SVN_K_CHEB = 1,      /* Chebyshev-Jacobi smoothing sweeps, all levels */
+  SVN_K_CHEB = 1,      /* Chebyshev-Jacobi smoothing sweeps on the finest level */
   SVN_K_MULTIDOT = 2,  /* FGMRES multi-dot (Arnoldi projections) */
   SVN_K_UPDATE = 3,    /* FGMRES update + norm */
   SVN_K_ELEMENT = 4,   /* element matrices of the linearisation */

@@ -86,6 +86,11 @@ struct svn_handle {
   cudaGraph_t vc_graph = nullptr;
   cudaGraphExec_t vc_exec = nullptr;
   cudaStream_t cap_stream = nullptr;   // private stream used only to record the graph
+  bool graph_dirty = false;            // re-record the graph before its next launch
+  bool graph_events = false;           // the recorded graph times its level-0 sweeps
+  bool recording = false;              // a V-cycle is being recorded
+  cudaEvent_t gev[64] = {};            // event pairs around level-0 sweeps (graph nodes)
+  int n_gev = 0;
 
   // instrumentation
   struct ProfRec {
@@ -323,6 +328,44 @@ int linearize(svn_handle* h, const double2* v, const double* pi) {
   return SVN_OK;
 }
 
+// Times level-0 Chebyshev sweeps: CUDA events around the launch, either as
+// ordinary records (eager V-cycle) or as event-record nodes of the graph.
+struct SweepTimer {
+  svn_handle* h;
+  int idx = -1;
+  Prof* pr = nullptr;
+  SweepTimer(svn_handle* hh, int level) : h(hh) {
+    if (level != 0) return;
+    if (h->recording) {
+      if (!h->graph_events || h->n_gev + 2 > 64) return;
+      idx = h->n_gev;
+      h->n_gev += 2;
+      for (int e = idx; e < idx + 2; ++e)
+        if (!h->gev[e]) cudaEventCreate(&h->gev[e]);
+      cudaEventRecordWithFlags(h->gev[idx], h->stream, cudaEventRecordExternal);
+    } else {
+      pr = new Prof(h, SVN_K_CHEB);
+    }
+  }
+  ~SweepTimer() {
+    if (idx >= 0) cudaEventRecordWithFlags(h->gev[idx + 1], h->stream, cudaEventRecordExternal);
+    delete pr;
+  }
+};
+
+// Accumulate the sweep times of the last graph launch (call after a sync).
+void collect_graph_events(svn_handle* h) {
+  if (!h->prof_on || !h->graph_events) return;
+  for (int e = 0; e + 1 < h->n_gev; e += 2) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, h->gev[e], h->gev[e + 1]) == cudaSuccess) {
+      h->prof_ms[SVN_K_CHEB] += ms;
+      h->prof_n[SVN_K_CHEB] += 1;
+    }
+  }
+  cudaGetLastError();
+}
+
 // One V-cycle on levels l..L-1: x_l = M_l^-1 b_l, both in level-l vectors (TV).
 template <typename TS, typename TD, typename TV>
 void vcycle(svn_handle* h, int l, const TV* b, TV* xout) {
@@ -347,7 +390,7 @@ void vcycle(svn_handle* h, int l, const TV* b, TV* xout) {
   TV* cur = x0;
   TV* nxt = x1;
   for (int k = 1; k < deg; ++k) {
-    Prof pr(h, SVN_K_CHEB);
+    SweepTimer tm(h, l);
     launch_cheb_sweep<TS, TD, TV>(s, lv.g, st, dinv, coef, k, cur, nxt, d, b);
     std::swap(cur, nxt);
   }
@@ -360,7 +403,7 @@ void vcycle(svn_handle* h, int l, const TV* b, TV* xout) {
   // post-smoothing (same polynomial), the last sweep writing xout when it can
   for (int k = 0; k < deg; ++k) {
     TV* dst = (k == deg - 1 && xout != cur) ? xout : (cur == x0 ? x1 : x0);
-    Prof pr(h, SVN_K_CHEB);
+    SweepTimer tm(h, l);
     launch_cheb_sweep<TS, TD, TV>(s, lv.g, st, dinv, coef, k, cur, dst, d, b);
     cur = dst;
   }
@@ -390,12 +433,22 @@ int precondition(svn_handle* h, const double2* r, double2* z) {
   CKL();
   Prof pr(h, SVN_K_VCYCLE);
   if (h->prm.use_graphs) {
+    if (h->graph_dirty && h->vc_exec) {
+      cudaGraphExecDestroy(h->vc_exec);
+      cudaGraphDestroy(h->vc_graph);
+      h->vc_exec = nullptr;
+      h->vc_graph = nullptr;
+    }
+    h->graph_dirty = false;
     if (!h->vc_exec) {
       // record on a private stream (the caller's stream may be the legacy
       // default stream, which cannot be captured); launch on the caller's
       if (!h->cap_stream) CK(cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking));
       const bool prof = h->prof_on;
-      h->prof_on = false;   // no event records inside the capture
+      h->prof_on = false;   // no ordinary event records inside the capture
+      h->graph_events = prof;
+      h->recording = true;
+      h->n_gev = 0;
       h->stream = h->cap_stream;
       cudaError_t e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
       if (e == cudaSuccess) {
@@ -403,6 +456,7 @@ int precondition(svn_handle* h, const double2* r, double2* z) {
         e = cudaStreamEndCapture(h->cap_stream, &h->vc_graph);
       }
       h->stream = s;
+      h->recording = false;
       h->prof_on = prof;
       if (e != cudaSuccess) return fail(h, SVN_ERR_CUDA, "V-cycle capture: %s", cudaGetErrorString(e));
       CK(cudaGraphInstantiate(&h->vc_exec, h->vc_graph, 0));
@@ -485,6 +539,7 @@ int fgmres(svn_handle* h, const double2* b, double2* x, double rtol, int maxit, 
         launch_sum_final(s, h->partial, nw, nr);
         CKL();
         TRY(sync_read(h, h->hbuf, hh.size(), hh.data()));
+        if (pass == 0) collect_graph_events(h);
         if (pass == 0) {
           for (int i = 0; i <= j; ++i) hh[m + 1 + i] = 0.0;
           double proj = 0.0;
@@ -654,6 +709,10 @@ void destroy_impl(svn_handle* h) {
   h->vc_graph = nullptr;
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   h->cap_stream = nullptr;
+  for (cudaEvent_t& e : h->gev) {
+    if (e) cudaEventDestroy(e);
+    e = nullptr;
+  }
   dfree(h->V); dfree(h->Z); dfree(h->hbuf); dfree(h->ybuf); dfree(h->partial); dfree(h->scal);
   if (h->hostbuf) cudaFreeHost(h->hostbuf);
   h->hostbuf = nullptr;
@@ -1006,6 +1065,7 @@ int svn_dual_update(svn_handle* h, double dt, const double* v, const double* dv,
 int svn_profile(svn_handle* h, int enable) {
   if (!h) return SVN_ERR_ARG;
   prof_collect(h);
+  if ((enable != 0) != h->prof_on) h->graph_dirty = true;   // re-record with / without sweep events
   if (enable) {
     for (int c = 0; c < SVN_K_COUNT; ++c) {
       h->prof_ms[c] = 0.0;
