@@ -87,6 +87,23 @@ def cpu_baseline_obj(N_full: int, steps: int = 1, warmup: int = 0) -> dict:
 
 
 # ---------------------------------------------------------------------------------------
+def max_over_ranks(value: float, world: int, device=None) -> float:
+    """Maximum of a per-rank number over the process group (the job's time)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate(tmax: float, steps: int, world: int) -> dict:
+    """Whole-job seconds per implicit step: every rank solves its own replica."""
+    return {"value": tmax / (steps * world), "ms_per_step": tmax / steps * 1000.0}
+
+
+# ---------------------------------------------------------------------------------------
 class ClockSampler:
     QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -126,6 +143,10 @@ class ClockSampler:
 SETTINGS = dict(eisenstat_walker=1, krylov_rtol=1e-4, ew_eta_max=0.1, max_krylov=600, cheb_degree=6,
                 cheb_lo=0.02, coarse_N=4, lmax_iters=15)
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2070 MHz
+# DRAM traffic (read + write) per node of the finest-level FP32 sweep, from the ncu
+# capture in profiles/k_cheb_sweep_fp32_1024.md (126.06 MB over 1,057,800 nodes);
+# set to None whenever k_cheb_sweep changes until it is captured again.
+SWEEP_TRAFFIC_PER_NODE = 126.06e6 / 1_057_800
 
 
 def sweep_bytes_per_node(mixed: bool, fp32_coef: bool) -> int:
@@ -183,10 +204,7 @@ def run_ours(args, rank, world):
     elapsed = e0.elapsed_time(e1) / 1000.0
     prof = {k: s.profile_read(k) for k in ("apply", "cheb", "multidot", "update", "element", "residual", "energy",
                                            "dual", "rap", "vcycle")}
-    tmax = torch.tensor([elapsed], dtype=torch.float64, device="cuda")
-    if world > 1:
-        torch.distributed.all_reduce(tmax, op=torch.distributed.ReduceOp.MAX)
-    tmax = float(tmax.item())
+    tmax = max_over_ranks(elapsed, world, device="cuda")
 
     # end to end through the C ABI with host buffers (pinned), copies inside
     e2e = None
@@ -202,11 +220,8 @@ def run_ours(args, rank, world):
         for _ in range(args.steps):
             s.set_forcing_host(*hn)
             s.step_host(p.dt, args.tol, out=host_out.numpy())
-        te = time.perf_counter() - t0
-        te_t = torch.tensor([te], dtype=torch.float64, device="cuda")
-        if world > 1:
-            torch.distributed.all_reduce(te_t, op=torch.distributed.ReduceOp.MAX)
-        e2e = {"value": float(te_t.item()) / (args.steps * world), "unit": UNIT,
+        te = max_over_ranks(time.perf_counter() - t0, world, device="cuda")
+        e2e = {"value": te / (args.steps * world), "unit": UNIT,
                "h2d_bytes_per_step": int(sum(x.numel() * 8 for x in host_in)),
                "d2h_bytes_per_step": int(host_out.numel() * 8)}
 
@@ -246,8 +261,11 @@ def run_ours(args, rank, world):
             roof = {"kernel": "k_cheb_sweep (finest-level Chebyshev-Jacobi sweep, %s)" % (
                         "FP32 stencil, FP32 vectors" if mixed else "FP64"),
                     "bound": "hbm", "achieved": ach, "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
-                    "frac": ach / hbm_peak, "traffic": None, "launches": n, "avg_us": avg_s * 1e6,
-                    "algorithmic_bytes_per_launch": byt}
+                    "frac": ach / hbm_peak,
+                    "traffic": (SWEEP_TRAFFIC_PER_NODE * (N + 1) * ((N + 1 + 7) // 8 * 8)
+                                if (mixed and SWEEP_TRAFFIC_PER_NODE) else None),
+                    "traffic_source": "ncu capture at 1024^2 scaled by nodes (profiles/k_cheb_sweep_fp32_1024.md)",
+                    "launches": n, "avg_us": avg_s * 1e6, "algorithmic_bytes_per_launch": byt}
         roof64 = None
         ms, n = prof["apply"]
         if n:
@@ -258,8 +276,8 @@ def run_ours(args, rank, world):
                       "avg_us": avg_s * 1e6, "launches": n, "hbm_gbs": 184.0 * nodes / avg_s / 1e9}
         shares = {k: round(prof[k][0] / 1000.0 / elapsed, 4) for k in prof}
         result = {
-            "metric": METRIC, "value": tmax / (args.steps * world), "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": tmax / args.steps * 1000.0,
+            "metric": METRIC, **aggregate(tmax, args.steps, world), "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
             "higher_is_better": False, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64+f32" if args.precision == "mixed" else "f64", "data": "synthetic",
             "config": workload_config(args, N),

@@ -9,7 +9,9 @@
 // All arithmetic runs in the CUDA kernels; the host only reads the handful of
 // scalars that steer the iteration (norms, energies, the Hessenberg column).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
+#include <thread>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -667,7 +669,7 @@ int create_impl(svn_handle* h, const svn_grid* g, const svn_params* p, void* str
     if (h->mixed && p->vcycle_fp32) TRY(dalloc(h, &L.st32, (size_t)NSTEN * lp));
     TRY(dalloc(h, (char**)&L.dinv, 3 * lp * (h->mixed ? sizeof(float) : sizeof(double))));
     TRY(dalloc(h, &L.lmax, 1));
-    TRY(dalloc(h, (double**)&L.cheb, 2 * (size_t)p->cheb_degree));
+    TRY(dalloc(h, (double**)&L.cheb, 2 * 16));
     for (int k = 0; k < 2; ++k) TRY(dalloc(h, (char**)&L.x[k], lp * vsz));
     TRY(dalloc(h, (char**)&L.d, lp * vsz));
     TRY(dalloc(h, (char**)&L.b, lp * vsz));
@@ -887,6 +889,7 @@ int svn_default_params(svn_params* p) {
   p->ew_eta_max = 0.1;
   p->lmax_iters = 15;
   p->lmax_safety = 1.15;
+  p->vcycle_fp32 = 1;
   return SVN_OK;
 }
 
@@ -1085,5 +1088,147 @@ int svn_profile_read(svn_handle* h, int kclass, double* ms_total, long long* lau
 }
 
 unsigned long long svn_kernel_launches(void) { return launches_issued(); }
+
+// ---- batched ensembles ------------------------------------------------------------
+// n independent instances (any mix of grid sizes), one handle and one private
+// non-blocking stream each; svn_batch_step drives them concurrently from a pool
+// of host threads so that small grids share the GPU.
+
+struct svn_batch {
+  std::vector<svn_handle*> hs;
+  std::vector<cudaStream_t> streams;
+  int device = 0;
+  int threads = 8;
+  std::string err;
+};
+
+int svn_batch_create(int n, const svn_grid* grids, const svn_params* p, int host_threads, svn_batch** out) {
+  if (!out) return SVN_ERR_ARG;
+  *out = nullptr;
+  if (n < 1 || n > 4096 || !grids || !p) return SVN_ERR_ARG;
+  svn_batch* b = new (std::nothrow) svn_batch();
+  if (!b) return SVN_ERR_OOM;
+  *out = b;
+  cudaGetDevice(&b->device);
+  b->threads = std::max(1, std::min(host_threads > 0 ? host_threads : 8, n));
+  for (int i = 0; i < n; ++i) {
+    cudaStream_t st = nullptr;
+    if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+      b->err = "stream creation failed";
+      return SVN_ERR_CUDA;
+    }
+    b->streams.push_back(st);
+    svn_handle* h = nullptr;
+    const int rc = svn_create(&grids[i], p, st, &h);
+    b->hs.push_back(h);
+    if (rc != SVN_OK) {
+      b->err = "instance " + std::to_string(i) + ": " + (h ? h->err : std::string("create failed"));
+      return rc;
+    }
+  }
+  return SVN_OK;
+}
+
+int svn_batch_destroy(svn_batch* b) {
+  if (!b) return SVN_ERR_ARG;
+  for (svn_handle* h : b->hs)
+    if (h) svn_destroy(h);
+  for (cudaStream_t s : b->streams)
+    if (s) cudaStreamDestroy(s);
+  delete b;
+  return SVN_OK;
+}
+
+const char* svn_batch_last_error(const svn_batch* b) { return b ? b->err.c_str() : "NULL batch"; }
+
+int svn_batch_size(const svn_batch* b) { return b ? (int)b->hs.size() : 0; }
+
+svn_handle* svn_batch_instance(svn_batch* b, int i) {
+  if (!b || i < 0 || i >= (int)b->hs.size()) return nullptr;
+  return b->hs[i];
+}
+
+int svn_batch_step(svn_batch* b, double dt, double tol, double* const* out_v, svn_stats* stats) {
+  if (!b || !out_v) return SVN_ERR_ARG;
+  const int n = (int)b->hs.size();
+  std::vector<int> rcs(n, SVN_OK);
+  std::atomic<int> next{0};
+  auto worker = [&]() {
+    cudaSetDevice(b->device);
+    for (int i = next.fetch_add(1); i < n; i = next.fetch_add(1))
+      rcs[i] = step_common(b->hs[i], dt, tol, out_v[i], stats ? &stats[i] : nullptr, false);
+  };
+  std::vector<std::thread> pool;
+  for (int t = 0; t < b->threads; ++t) pool.emplace_back(worker);
+  for (auto& t : pool) t.join();
+  for (int i = 0; i < n; ++i)
+    if (rcs[i] != SVN_OK) {
+      b->err = "instance " + std::to_string(i) + ": " + b->hs[i]->err;
+      return rcs[i];
+    }
+  return SVN_OK;
+}
+
+// ---- autotuner --------------------------------------------------------------------
+// Times FGMRES on the linearisation reached after `probe_newton` Newton
+// iterations of the current forcing, for every (degree, lo) candidate, and
+// keeps the fastest in the handle's parameters.
+int svn_autotune(svn_handle* h, double dt, int probe_newton, const int* degrees, int nd, const double* los, int nl,
+                 double* best_ms) {
+  if (!h || !degrees || !los || nd < 1 || nl < 1) return SVN_ERR_ARG;
+  for (int i = 0; i < nd; ++i)
+    if (degrees[i] < 1 || degrees[i] > 16) return fail(h, SVN_ERR_ARG, "degree out of range");
+  for (int i = 0; i < nl; ++i)
+    if (!(los[i] > 0.0 && los[i] < 1.0)) return fail(h, SVN_ERR_ARG, "lo out of range");
+  svn_params saved = h->prm;
+  svn_stats st;
+  memset(&st, 0, sizeof(st));
+  h->prm.max_newton = std::max(1, probe_newton);
+  step_impl(h, dt, 1e-300, &st);   // ends with SVN_ERR_NO_CONVERGENCE by design
+  h->prm = saved;
+  TRY(precompute(h, dt));
+  TRY(residual(h, h->v, h->R, &st.res_final));
+  launch_neg_copy(h->stream, h->g0, h->R, h->rhs);
+  CKL();
+  double best = 1e300;
+  int bd = saved.cheb_degree;
+  double bl = saved.cheb_lo;
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  for (int a = 0; a < nd; ++a)
+    for (int c = 0; c < nl; ++c) {
+      h->prm.cheb_degree = degrees[a];
+      h->prm.cheb_lo = los[c];
+      h->graph_dirty = true;
+      TRY(linearize(h, h->v, h->pi));
+      int its = 0;
+      TRY(fgmres(h, h->rhs, h->dv, saved.krylov_rtol, saved.max_krylov, &its));   // warm (records the graph)
+      CK(cudaEventRecord(e0, h->stream));
+      TRY(fgmres(h, h->rhs, h->dv, saved.krylov_rtol, saved.max_krylov, &its));
+      CK(cudaEventRecord(e1, h->stream));
+      CK(cudaEventSynchronize(e1));
+      float ms = 0.f;
+      CK(cudaEventElapsedTime(&ms, e0, e1));
+      if (ms < best) {
+        best = ms;
+        bd = degrees[a];
+        bl = los[c];
+      }
+    }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  h->prm.cheb_degree = bd;
+  h->prm.cheb_lo = bl;
+  h->graph_dirty = true;
+  if (best_ms) *best_ms = best;
+  return SVN_OK;
+}
+
+int svn_get_params(const svn_handle* h, svn_params* p) {
+  if (!h || !p) return SVN_ERR_ARG;
+  *p = h->prm;
+  return SVN_OK;
+}
 
 }  // extern "C"

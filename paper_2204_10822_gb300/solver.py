@@ -163,6 +163,19 @@ class Solver:
         self._check(self.lib.svn_krylov_solve(self.h, _ptr(b), _ptr(x), rtol, ctypes.byref(its)))
         return x, its.value
 
+    # -- autotuner ---------------------------------------------------------------
+    def autotune(self, dt: float, probe_newton: int = 4, degrees=(2, 3, 4, 6), los=(0.02, 0.05)):
+        """Pick the fastest Chebyshev (degree, lo) for this grid and forcing."""
+        d = (ctypes.c_int * len(degrees))(*degrees)
+        l = (ctypes.c_double * len(los))(*los)
+        best = ctypes.c_double()
+        self._check(self.lib.svn_autotune(self.h, dt, probe_newton, d, len(degrees), l, len(los),
+                                          ctypes.byref(best)))
+        p = capi.SvnParams()
+        self._check(self.lib.svn_get_params(self.h, ctypes.byref(p)))
+        self.params = p
+        return {"cheb_degree": p.cheb_degree, "cheb_lo": p.cheb_lo, "ms": best.value}
+
     # -- instrumentation -------------------------------------------------------
     def profile(self, enable: bool):
         self._check(self.lib.svn_profile(self.h, 1 if enable else 0))
@@ -180,3 +193,57 @@ class Solver:
     def dual_update(self, dt: float, v, dv, alpha: float, pi):
         self._check(self.lib.svn_dual_update(self.h, dt, _ptr(v), _ptr(dv), alpha, _ptr(pi)))
         return pi
+
+
+class Batch:
+    """An ensemble of independent instances (any grid sizes), stepped concurrently."""
+
+    def __init__(self, Ns, L: float = 512e3, host_threads: int = 8, **params):
+        import torch
+        self.lib = capi.lib()
+        self.Ns = [int(n) for n in Ns]
+        self.L = float(L)
+        self.params = default_params(**params)
+        grids = (capi.SvnGrid * len(self.Ns))(*[capi.SvnGrid(n, self.L) for n in self.Ns])
+        h = ctypes.c_void_p()
+        torch.cuda.current_stream().synchronize()
+        rc = self.lib.svn_batch_create(len(self.Ns), grids, ctypes.byref(self.params), host_threads, ctypes.byref(h))
+        self.b = h
+        if rc != 0:
+            msg = self.lib.svn_batch_last_error(h).decode() if h.value else ""
+            if h.value:
+                self.lib.svn_batch_destroy(h)
+            self.b = None
+            raise SvnError(rc, msg)
+        self.handles = [ctypes.c_void_p(self.lib.svn_batch_instance(self.b, i)) for i in range(len(self.Ns))]
+
+    def close(self):
+        if getattr(self, "b", None):
+            self.lib.svn_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_forcing(self, i, h, A, wind, ocean, v_old):
+        import torch
+        torch.cuda.current_stream().synchronize()      # inputs are read on the instance's own stream
+        rc = self.lib.svn_set_forcing(self.handles[i], _ptr(h), _ptr(A), _ptr(wind), _ptr(ocean), _ptr(v_old))
+        if rc != 0:
+            raise SvnError(rc, self.lib.svn_last_error(self.handles[i]).decode())
+
+    def step(self, dt: float, tol: float, outs=None):
+        import torch
+        n = len(self.Ns)
+        if outs is None:
+            outs = [torch.zeros((N + 1, N + 1, 2), dtype=torch.float64, device="cuda") for N in self.Ns]
+        torch.cuda.current_stream().synchronize()
+        ptrs = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
+        stats = (capi.SvnStats * n)()
+        rc = self.lib.svn_batch_step(self.b, dt, tol, ptrs, stats)
+        if rc != 0:
+            raise SvnError(rc, self.lib.svn_batch_last_error(self.b).decode())
+        return outs, [s.to_dict() for s in stats]

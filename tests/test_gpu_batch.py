@@ -1,0 +1,51 @@
+"""Batched ensembles and the autotuner (GPU).
+
+Each ensemble member is an independent implicit step, so the batch must give
+exactly what a single solver gives for the same inputs (same kernels, same
+order of operations), and the members must match the FP64 oracle.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.newton import newton
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def test_batch_matches_single_instances_and_oracle():
+    from paper_2204_10822_gb300 import Batch, Solver
+    Ns = [16, 32, 24, 64, 16]
+    probs = [W.make_problem(N, seed=100 + i) for i, N in enumerate(Ns)]
+    b = Batch(Ns, host_threads=3)
+    for i, p in enumerate(probs):
+        b.set_forcing(i, dev(p.h), dev(p.A), dev(p.wind), dev(p.ocean), dev(p.v_old))
+    outs, stats = b.step(1800.0, 1e-10)
+    for i, p in enumerate(probs):
+        s = Solver(p.N, p.L)
+        s.set_forcing(dev(p.h), dev(p.A), dev(p.wind), dev(p.ocean), dev(p.v_old))
+        v, st = s.step(1800.0, 1e-10)
+        assert st["newton_iters"] == stats[i]["newton_iters"]
+        assert np.array_equal(v.cpu().numpy(), outs[i].cpu().numpy())
+        s.close()
+    ref = newton(probs[3], tol=1e-10)
+    v3 = outs[3].cpu().numpy()
+    assert np.linalg.norm(v3 - ref.v) <= 1e-8 * np.linalg.norm(ref.v)
+    b.close()
+
+
+def test_autotune_picks_a_candidate_and_still_solves():
+    from paper_2204_10822_gb300 import Solver
+    p = W.config(0, N=64)
+    s = Solver(p.N, p.L, precision="mixed")
+    s.set_forcing(dev(p.h), dev(p.A), dev(p.wind), dev(p.ocean), dev(p.v_old))
+    best = s.autotune(p.dt, probe_newton=3, degrees=(2, 4), los=(0.02, 0.1))
+    assert best["cheb_degree"] in (2, 4) and best["cheb_lo"] in (0.02, 0.1) and best["ms"] > 0
+    ref = newton(p, tol=1e-10)
+    v, st = s.step(p.dt, 1e-10)
+    assert np.linalg.norm(v.cpu().numpy() - ref.v) <= 1e-6 * np.linalg.norm(ref.v)

@@ -185,13 +185,15 @@ def test_step_parity_fp64(N):
     assert stats["status"] == "SVN_OK"
 
 
-def test_step_parity_mixed():
+@pytest.mark.parametrize("fp32", [1, 0])
+def test_step_parity_mixed(fp32):
     p = W.config(0, N=64)
     res = newton(p, tol=1e-10)
-    s = make_solver(p, precision="mixed")
+    s = make_solver(p, precision="mixed", vcycle_fp32=fp32)
     v, stats = s.step(p.dt, 1e-10)
     err = np.linalg.norm(host(v) - res.v) / np.linalg.norm(res.v)
     assert err <= 1e-6, err
+    assert abs(stats["newton_iters"] - res.newton_iters) <= 1
 
 
 def test_step_nonzero_v_old_and_state_roundtrip():
