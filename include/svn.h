@@ -62,7 +62,8 @@ enum svn_status {
 enum svn_precision {
   SVN_FP64 = 0,   /* every kernel in FP64 (the plain path) */
   SVN_MIXED = 1   /* FP64 residual, energy, dual update, outer FGMRES and its
-                     operator; FP32 V-cycle on BF16-stored coefficients */
+                     operator; FP32 V-cycle on FP32-stored (vcycle_fp32 = 1,
+                     default) or BF16-stored stencils */
 };
 
 typedef struct svn_grid {
@@ -94,8 +95,10 @@ typedef struct svn_params {
   int lmax_iters;           /* power-method steps for lambda_max(D^-1 A) per level
                                (0: Gershgorin bound) */
   double lmax_safety;       /* the estimate is multiplied by this factor */
-  int vcycle_fp32;          /* mixed precision: 1 stores the V-cycle stencils in FP32
-                               instead of BF16 */
+  int vcycle_fp32;          /* mixed precision: 1 (default) stores the V-cycle stencils
+                               in FP32, 0 in BF16 (BF16 rounding of the entries
+                               perturbs the near-rigid modes; robust only on
+                               coarse grids) */
 } svn_params;
 
 typedef struct svn_stats {
@@ -185,6 +188,31 @@ int svn_krylov_solve(svn_handle* h, const double* b, double* x, double rtol, int
  * modification of Eq. "modification"), in place on the device array pi. */
 int svn_dual_update(svn_handle* h, double dt, const double* v, const double* dv,
                     double alpha, double* pi);
+
+/* ---- Ensembles (no counterpart in the paper: the paper solves one
+ * instance at a time).  n independent instances of any grid sizes; each
+ * has its own handle and private non-blocking stream, and svn_batch_step
+ * advances all of them by one implicit step concurrently from host_threads
+ * host threads (<= 0: 8), so that small grids share the GPU.  out_v[i] are
+ * device node vectors of instance i's grid; stats (may be NULL) is an array
+ * of n.  The first failing instance's code is returned. ---- */
+typedef struct svn_batch svn_batch;
+int svn_batch_create(int n, const svn_grid* grids, const svn_params* p, int host_threads, svn_batch** out);
+int svn_batch_destroy(svn_batch* b);
+const char* svn_batch_last_error(const svn_batch* b);
+int svn_batch_size(const svn_batch* b);
+/* Handle of instance i (owned by the batch): use it with svn_set_forcing etc. */
+svn_handle* svn_batch_instance(svn_batch* b, int i);
+int svn_batch_step(svn_batch* b, double dt, double tol, double* const* out_v, svn_stats* stats);
+
+/* ---- Autotuner (no counterpart in the paper).  Runs probe_newton Newton
+ * iterations of the current forcing, then times one FGMRES solve of that
+ * linearisation for every (degree, lo) pair of Chebyshev smoother settings
+ * and keeps the fastest in the handle's parameters (read them back with
+ * svn_get_params).  *best_ms (may be NULL) receives the winning time. ---- */
+int svn_autotune(svn_handle* h, double dt, int probe_newton, const int* degrees, int nd,
+                 const double* los, int nl, double* best_ms);
+int svn_get_params(const svn_handle* h, svn_params* p);
 
 /* ---- Instrumentation (no counterpart in the paper): CUDA-event timing of
  * one kernel class on the handle's stream, for roofline reporting. ---- */

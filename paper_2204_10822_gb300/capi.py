@@ -74,6 +74,15 @@ _SIGS = {
     "svn_profile": (c_int, [c_void_p, c_int]),
     "svn_profile_read": (c_int, [c_void_p, c_int, P_double, ctypes.POINTER(ctypes.c_longlong)]),
     "svn_kernel_launches": (ctypes.c_ulonglong, []),
+    "svn_batch_create": (c_int, [c_int, ctypes.POINTER(SvnGrid), ctypes.POINTER(SvnParams), c_int,
+                                 ctypes.POINTER(c_void_p)]),
+    "svn_batch_destroy": (c_int, [c_void_p]),
+    "svn_batch_last_error": (ctypes.c_char_p, [c_void_p]),
+    "svn_batch_size": (c_int, [c_void_p]),
+    "svn_batch_instance": (c_void_p, [c_void_p, c_int]),
+    "svn_batch_step": (c_int, [c_void_p, c_double, c_double, ctypes.POINTER(c_void_p), ctypes.POINTER(SvnStats)]),
+    "svn_autotune": (c_int, [c_void_p, c_double, c_int, ctypes.POINTER(c_int), c_int, P_double, c_int, P_double]),
+    "svn_get_params": (c_int, [c_void_p, ctypes.POINTER(SvnParams)]),
 }
 
 KCLASS = {"apply": 0, "cheb": 1, "multidot": 2, "update": 3, "element": 4, "residual": 5, "energy": 6,
