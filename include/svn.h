@@ -189,6 +189,35 @@ int svn_krylov_solve(svn_handle* h, const double* b, double* x, double rtol, int
 int svn_dual_update(svn_handle* h, double dt, const double* v, const double* dv,
                     double alpha, double* pi);
 
+/* ---- Allocation-free residual.  The paper has no counterpart: this entry
+ * point exists for callers that cannot call cudaMalloc -- for example a host
+ * model that hands the whole device to its own memory pool at start-up, or a
+ * runtime that keeps its device footprint fixed after initialisation.  It
+ * computes the same R(v) and ||R|| as svn_residual, without a handle:
+ *   grid, prm     : grid (even N, 8 <= N <= SVN_NOALLOC_MAX_N) and constants;
+ *   dt            : time step [s], > 0;
+ *   hcell .. v_old: device inputs in the layouts above (as svn_set_forcing);
+ *   v             : device node vector at which R is evaluated;
+ *   R             : device node vector receiving R(v) (boundary entries 0);
+ *   norm          : host double receiving ||R|| (may be NULL: then the call
+ *                   does not synchronise the stream);
+ *   cuda_stream   : cudaStream_t the work is ordered on (NULL = default).
+ * It allocates nothing: every intermediate array lives in one file-scope
+ * device array of about 16 MB (30 planes of the N = SVN_NOALLOC_MAX_N
+ * layout), which every GPU that loads the library holds until the process
+ * exits.  The first call on a device looks up that array's address (once per
+ * device, with the device current); make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents:
+ * calls that overlap on the GPU (several streams or host threads) race.
+ * Returns SVN_ERR_ARG for N above the maximum, odd N or bad constants,
+ * SVN_ERR_NONFINITE for a non-finite norm, SVN_ERR_CUDA on a CUDA error;
+ * there is no handle, so no message is recorded. ---- */
+#define SVN_NOALLOC_MAX_N 256
+int svn_residual_noalloc(const svn_grid* grid, const svn_params* prm, double dt,
+                         const double* hcell, const double* A, const double* wind,
+                         const double* ocean, const double* v_old, const double* v,
+                         double* R, double* norm, void* cuda_stream);
+
 /* ---- Ensembles (no counterpart in the paper: the paper solves one
  * instance at a time).  n independent instances of any grid sizes; each
  * has its own handle and private non-blocking stream, and svn_batch_step

@@ -83,6 +83,8 @@ _SIGS = {
     "svn_batch_step": (c_int, [c_void_p, c_double, c_double, ctypes.POINTER(c_void_p), ctypes.POINTER(SvnStats)]),
     "svn_autotune": (c_int, [c_void_p, c_double, c_int, ctypes.POINTER(c_int), c_int, P_double, c_int, P_double]),
     "svn_get_params": (c_int, [c_void_p, ctypes.POINTER(SvnParams)]),
+    "svn_residual_noalloc": (c_int, [ctypes.POINTER(SvnGrid), ctypes.POINTER(SvnParams), c_double] +
+                             [c_void_p] * 7 + [P_double, c_void_p]),
 }
 
 KCLASS = {"apply": 0, "cheb": 1, "multidot": 2, "update": 3, "element": 4, "residual": 5, "energy": 6,
