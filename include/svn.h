@@ -95,6 +95,8 @@ typedef struct svn_params {
   int lmax_iters;           /* power-method steps for lambda_max(D^-1 A) per level
                                (0: Gershgorin bound) */
   double lmax_safety;       /* the estimate is multiplied by this factor */
+  int fused_trial;          /* 1 (default): evaluate Phi, R and pi at the unit step in one
+                               fused pass; 0: separate energy / residual / dual passes */
   int vcycle_fp32;          /* mixed precision: 1 (default) stores the V-cycle stencils
                                in FP32, 0 in BF16 (BF16 rounding of the entries
                                perturbs the near-rigid modes; robust only on

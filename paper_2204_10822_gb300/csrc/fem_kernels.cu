@@ -342,11 +342,59 @@ __global__ void k_energy_final(int k, const double* __restrict__ partial, int nb
 // the mass tensor M = rho H I + dt Co rho_o (|w| I + w w^T / |w|) (Eq.
 // "standardNewton2"; the rank-one term is dropped for |w| < 1e-14 m/s), and
 // the element matrix K_e = sum_q w (N^T M N + B^T C B), upper triangle.
+//
+// Evaluation.  On the uniform grid the hat derivatives of the Q1 basis at a
+// Gauss point are dN_c/dxi = sx_c G(b_c, qb), dN_c/deta = sy_c G(a_c, qa) with
+// G(b, q) = g1 if b == q else g0 (sx, sy = -+1 for corner bits a, b = 0, 1),
+// and N_c = G(a_c, qa) G(b_c, qb).  With u = (ta, tb, 0), u' = (tb, ta, 0),
+// e2 = (0, 0, sqrt2 tc) and C' = C / 4 (hat-unit weight w / dx^2), the six
+// scalars A1 = u C' u, A2 = u C' e2, A3 = e2 C' e2, A4 = u' C' u', A5 = u' C' e2,
+// A6 = u C' u' give
+//   Kxx[c][d] = sum_q A1 dxi_c dxi_d + A2 (dxi_c deta_d + deta_c dxi_d) + A3 deta_c deta_d
+//   Kyy[c][d] = sum_q A4 deta_c deta_d + A5 (deta_c dxi_d + dxi_c deta_d) + A3 dxi_c dxi_d
+//   Kxy[c][d] = sum_q A6 dxi_c deta_d + A2 dxi_c dxi_d + A5 deta_c deta_d + A3 deta_c dxi_d
+// (plus the mass terms sum_q N_c N_d w M), so each entry is a signed sum of a
+// few small "moment tables" of the six scalars over the four points.
+__device__ __forceinline__ double gq(int b, int q) { return b == q ? GQ1 : GQ0; }
+
+struct Moments {
+  double xx[3];      // T_xixi[bc][bd]: [0][0], [0][1], [1][1]
+  double ee[3];      // T_etaeta[ac][ad]
+  double xe[2][2];   // T_xieta[bc][ad]
+};
+
+__device__ __forceinline__ void moments(const double F[4], Moments& m) {
+  // q = qa + 2 qb
+  const double fb0 = F[0] + F[1], fb1 = F[2] + F[3];   // sums over qa, per qb
+  const double fa0 = F[0] + F[2], fa1 = F[1] + F[3];   // sums over qb, per qa
+  const double g00 = GQ0 * GQ0, g11 = GQ1 * GQ1, g01 = GQ0 * GQ1;
+  // T_xixi[bc][bd] = sum_qb G(bc,qb) G(bd,qb) fb(qb)
+  m.xx[0] = g11 * fb0 + g00 * fb1;
+  m.xx[1] = g01 * (fb0 + fb1);
+  m.xx[2] = g00 * fb0 + g11 * fb1;
+  m.ee[0] = g11 * fa0 + g00 * fa1;
+  m.ee[1] = g01 * (fa0 + fa1);
+  m.ee[2] = g00 * fa0 + g11 * fa1;
+#pragma unroll
+  for (int bc = 0; bc < 2; ++bc)
+#pragma unroll
+    for (int ad = 0; ad < 2; ++ad) {
+      double t = 0.0;
+#pragma unroll
+      for (int qb = 0; qb < 2; ++qb)
+#pragma unroll
+        for (int qa = 0; qa < 2; ++qa) t += gq(bc, qb) * gq(ad, qa) * F[qa + 2 * qb];
+      m.xe[bc][ad] = t;
+    }
+}
+
+__device__ __forceinline__ double sym2(const double t[3], int i, int j) { return t[i + j]; }
+
 template <typename TE>
-__global__ void k_element_matrices(Layout g, Phys ph, const double2* __restrict__ v,
-                                   const double* __restrict__ pi, const double* __restrict__ P,
-                                   const double* __restrict__ rhoH, const double* __restrict__ voq,
-                                   TE* __restrict__ ke, float* __restrict__ qcoef) {
+__global__ void __launch_bounds__(128) k_element_matrices(Layout g, Phys ph, const double2* __restrict__ v,
+                                                          const double* __restrict__ pi, const double* __restrict__ P,
+                                                          const double* __restrict__ rhoH,
+                                                          const double* __restrict__ voq, TE* __restrict__ ke) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   if (i >= g.N || j >= g.N) return;
@@ -356,86 +404,84 @@ __global__ void k_element_matrices(Layout g, Phys ph, const double2* __restrict_
   const double rh = rhoH[cell];
   const double idx = 1.0 / ph.dx;
   const double sq2 = 1.4142135623730950488;
-  double K[NELEM];
+  const double ta = ph.ta, tb = ph.tb, s2 = sq2 * ph.tc;
+  double A1[4], A2[4], A3[4], A4[4], A5[4], A6[4], Mxx[4], Myy[4], Mxy[4];
 #pragma unroll
-  for (int e = 0; e < NELEM; ++e) K[e] = 0.0;
-#pragma unroll 1
   for (int q = 0; q < 4; ++q) {
-    const double xi = qxi(q), eta = qeta(q);
-    const Qp p = eval_qp(c, xi, eta);
+    const Qp p = eval_qp(c, qxi(q), qeta(q));
     double txx, tyy, txy;
     tau_hat(ph, p, txx, tyy, txy);
     const double t0 = txx * idx, t1 = tyy * idx, t2 = sq2 * txy * idx;   // Voigt tau
-    const double d2 = ph.dmin2 + 2.0 * (t0 * t0 + t1 * t1 + t2 * t2);
-    const double inv = rsqrt(d2);
+    const double inv = rsqrt(ph.dmin2 + 2.0 * (t0 * t0 + t1 * t1 + t2 * t2));
     const double p0 = pi[(3 * q + 0) * g.plane + cell];
     const double p1 = pi[(3 * q + 1) * g.plane + cell];
     const double p2 = sq2 * pi[(3 * q + 2) * g.plane + cell];
-    const double pp = p0 * p0 + p1 * p1 + p2 * p2;
-    const double m = fmax(1.0, sqrt(2.0 * pp));                        // FP64 branch
-    const double a = ph.dt * Pc * inv;                                 // dt P / Delta
-    const double b = ph.dt * Pc * inv * inv / m;                       // dt P / (Delta^2 m)
-    // C = a I - b (t p^T + p t^T), symmetric
+    const double m = fmax(1.0, sqrt(2.0 * (p0 * p0 + p1 * p1 + p2 * p2)));   // FP64 branch
+    const double a = 0.25 * ph.dt * Pc * inv;               // C' = C / 4
+    const double b = 0.25 * ph.dt * Pc * inv * inv / m;
     const double C00 = a - 2.0 * b * t0 * p0, C11 = a - 2.0 * b * t1 * p1, C22 = a - 2.0 * b * t2 * p2;
     const double C01 = -b * (t0 * p1 + p0 * t1), C02 = -b * (t0 * p2 + p0 * t2), C12 = -b * (t1 * p2 + p1 * t2);
-    // mass tensor
+    A1[q] = ta * ta * C00 + 2.0 * ta * tb * C01 + tb * tb * C11;
+    A4[q] = tb * tb * C00 + 2.0 * ta * tb * C01 + ta * ta * C11;
+    A6[q] = ta * tb * (C00 + C11) + (ta * ta + tb * tb) * C01;
+    A2[q] = s2 * (ta * C02 + tb * C12);
+    A5[q] = s2 * (tb * C02 + ta * C12);
+    A3[q] = s2 * s2 * C22;
     const double wx = voq[(2 * q) * g.plane + cell] - p.vx;
     const double wy = voq[(2 * q + 1) * g.plane + cell] - p.vy;
-    const double nw2 = wx * wx + wy * wy;
-    const double nw = sqrt(nw2);
+    const double nw = sqrt(wx * wx + wy * wy);
     const double od = ph.dt * ph.cdrag;
-    double Mxx = rh + od * nw, Myy = rh + od * nw, Mxy = 0.0;
+    double mxx = rh + od * nw, myy = rh + od * nw, mxy = 0.0;
     if (nw >= 1e-14) {
       const double r1 = od / nw;
-      Mxx += r1 * wx * wx;
-      Myy += r1 * wy * wy;
-      Mxy = r1 * wx * wy;
+      mxx += r1 * wx * wx;
+      myy += r1 * wy * wy;
+      mxy = r1 * wx * wy;
     }
-    if (qcoef != nullptr) {
-      float* qc = qcoef + (long long)(NQCOEF * q) * g.plane + cell;
-      qc[0 * g.plane] = (float)C00; qc[1 * g.plane] = (float)C11; qc[2 * g.plane] = (float)C22;
-      qc[3 * g.plane] = (float)C01; qc[4 * g.plane] = (float)C02; qc[5 * g.plane] = (float)C12;
-      qc[6 * g.plane] = (float)Mxx; qc[7 * g.plane] = (float)Myy; qc[8 * g.plane] = (float)Mxy;
-    }
-    // basis vectors: value n[c], hat tau Voigt of N_c e_x and N_c e_y
-    double n[4], bx[4][3], by[4][3];
+    Mxx[q] = ph.w * mxx;
+    Myy[q] = ph.w * myy;
+    Mxy[q] = ph.w * mxy;
+  }
+  Moments mA1, mA2, mA3, mA4, mA5, mA6;
+  moments(A1, mA1);
+  moments(A2, mA2);
+  moments(A3, mA3);
+  moments(A4, mA4);
+  moments(A5, mA5);
+  moments(A6, mA6);
 #pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
-      double dxi, deta;
-      shape(cc, xi, eta, n[cc], dxi, deta);
-      bx[cc][0] = ph.ta * dxi; bx[cc][1] = ph.tb * dxi; bx[cc][2] = sq2 * ph.tc * deta;
-      by[cc][0] = ph.tb * deta; by[cc][1] = ph.ta * deta; by[cc][2] = sq2 * ph.tc * dxi;
-    }
-    // stiffness weight: w / dx^2 = 1/4; mass weight w
-    double Bv[8][3], CB[8][3];
+  for (int cc = 0; cc < 4; ++cc) {
 #pragma unroll
-    for (int cc = 0; cc < 4; ++cc) {
+    for (int dd = cc; dd < 4; ++dd) {
+      const int ac = cc & 1, bc = cc >> 1, ad = dd & 1, bd = dd >> 1;
+      const double sxc = ac ? 1.0 : -1.0, syc = bc ? 1.0 : -1.0, sxd = ad ? 1.0 : -1.0, syd = bd ? 1.0 : -1.0;
+      // mass moments: sum_q N_c N_d M(q)
+      double nxx = 0.0, nyy = 0.0, nxy = 0.0;
 #pragma unroll
-      for (int s = 0; s < 3; ++s) {
-        Bv[2 * cc][s] = bx[cc][s];
-        Bv[2 * cc + 1][s] = by[cc][s];
+      for (int q = 0; q < 4; ++q) {
+        const int qa = q & 1, qb = q >> 1;
+        const double nn = gq(ac, qa) * gq(bc, qb) * gq(ad, qa) * gq(bd, qb);
+        nxx += nn * Mxx[q];
+        nyy += nn * Myy[q];
+        nxy += nn * Mxy[q];
       }
-    }
-#pragma unroll
-    for (int d = 0; d < 8; ++d) {
-      CB[d][0] = 0.25 * (C00 * Bv[d][0] + C01 * Bv[d][1] + C02 * Bv[d][2]);
-      CB[d][1] = 0.25 * (C01 * Bv[d][0] + C11 * Bv[d][1] + C12 * Bv[d][2]);
-      CB[d][2] = 0.25 * (C02 * Bv[d][0] + C12 * Bv[d][1] + C22 * Bv[d][2]);
-    }
-#pragma unroll
-    for (int r = 0; r < 8; ++r) {
-#pragma unroll
-      for (int s = r; s < 8; ++s) {
-        double val = Bv[r][0] * CB[s][0] + Bv[r][1] * CB[s][1] + Bv[r][2] * CB[s][2];
-        const int kr = r & 1, ks = s & 1;
-        const double mkl = (kr == ks) ? (kr == 0 ? Mxx : Myy) : Mxy;
-        val += ph.w * n[r >> 1] * n[s >> 1] * mkl;
-        K[elem_index(r, s)] += val;
+      const double kxx = sxc * sxd * sym2(mA1.xx, bc, bd) + sxc * syd * mA2.xe[bc][ad] +
+                         syc * sxd * mA2.xe[bd][ac] + syc * syd * sym2(mA3.ee, ac, ad) + nxx;
+      const double kyy = syc * syd * sym2(mA4.ee, ac, ad) + syc * sxd * mA5.xe[bd][ac] +
+                         sxc * syd * mA5.xe[bc][ad] + sxc * sxd * sym2(mA3.xx, bc, bd) + nyy;
+      const double kxy = sxc * syd * mA6.xe[bc][ad] + sxc * sxd * sym2(mA2.xx, bc, bd) +
+                         syc * syd * sym2(mA5.ee, ac, ad) + syc * sxd * mA3.xe[bd][ac] + nxy;
+      ke[(long long)elem_index(2 * cc, 2 * dd) * g.plane + cell] = (TE)kxx;
+      ke[(long long)elem_index(2 * cc + 1, 2 * dd + 1) * g.plane + cell] = (TE)kyy;
+      ke[(long long)elem_index(2 * cc, 2 * dd + 1) * g.plane + cell] = (TE)kxy;
+      if (dd != cc) {
+        // K[2cc+1][2dd] = Kyx[cc][dd] = Kxy[dd][cc]
+        const double kyx = sxd * syc * mA6.xe[bd][ac] + sxd * sxc * sym2(mA2.xx, bd, bc) +
+                           syd * syc * sym2(mA5.ee, ad, ac) + syd * sxc * mA3.xe[bc][ad] + nxy;
+        ke[(long long)elem_index(2 * cc + 1, 2 * dd) * g.plane + cell] = (TE)kyx;
       }
     }
   }
-#pragma unroll
-  for (int e = 0; e < NELEM; ++e) ke[e * g.plane + cell] = (TE)K[e];
 }
 
 // Element-matrix entry (r, s) of cell `cell`, either triangle.
@@ -539,6 +585,128 @@ __global__ void k_dual_update(Layout g, Phys ph, double alpha, const double2* __
   }
 }
 
+// ---- fused trial point (a8 + a2 + a9 at alpha = 1) ---------------------------------------
+// One pass over the cells evaluates, at u = v + dv:
+//   * the energy contributions (compensated, as k_energy_cells) and sum |terms|,
+//   * the residual cell contributions of R(u) into eb (as k_residual_cells),
+//   * the trial dual state pi_t = pi + pi~(v, dv, pi) (as k_dual_update with alpha = 1),
+// so that an accepted unit step needs no further pass.
+__global__ void k_trial_cells(Layout g, Phys ph, const double2* __restrict__ v, const double2* __restrict__ dv,
+                              const double* __restrict__ P, const double* __restrict__ rhoH,
+                              const double* __restrict__ fq, const double* __restrict__ voq,
+                              const double* __restrict__ pi, double* __restrict__ pi_t, double* __restrict__ eb,
+                              double* __restrict__ partial, int nblocks) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  const int bid = blockIdx.y * gridDim.x + blockIdx.x;
+  DD acc{0.0, 0.0};
+  double asum = 0.0;
+  if (i < g.N && j < g.N) {
+    const long long cell = (long long)j * g.ld + i;
+    const Corners c0 = load_corners(v, cell, g.ld);
+    const Corners d0 = load_corners(dv, cell, g.ld);
+    Corners c;
+    c.v00 = make_double2(c0.v00.x + d0.v00.x, c0.v00.y + d0.v00.y);
+    c.v10 = make_double2(c0.v10.x + d0.v10.x, c0.v10.y + d0.v10.y);
+    c.v01 = make_double2(c0.v01.x + d0.v01.x, c0.v01.y + d0.v01.y);
+    c.v11 = make_double2(c0.v11.x + d0.v11.x, c0.v11.y + d0.v11.y);
+    const double Pdt = ph.dt * P[cell];
+    const double rh = rhoH[cell];
+    const double idx = 1.0 / ph.dx;
+    const double vpw = 0.25 * ph.dx;
+    const double sq2 = 1.4142135623730950488;
+    double rx[4] = {0, 0, 0, 0}, ry[4] = {0, 0, 0, 0};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const double xi = qxi(q), eta = qeta(q);
+      // dual step at the current point (uses tau(v), Delta(v), tau(dv))
+      {
+        const Qp pv = eval_qp(c0, xi, eta);
+        const Qp pd = eval_qp(d0, xi, eta);
+        double txx, tyy, txy, sxx, syy, sxy;
+        tau_hat(ph, pv, txx, tyy, txy);
+        tau_hat(ph, pd, sxx, syy, sxy);
+        const double t0 = txx * idx, t1 = tyy * idx, t2 = sq2 * txy * idx;
+        const double s0 = sxx * idx, s1 = syy * idx, s2 = sq2 * sxy * idx;
+        const double inv = rsqrt(ph.dmin2 + 2.0 * (t0 * t0 + t1 * t1 + t2 * t2));
+        const double* pq = pi + (long long)(3 * q) * g.plane + cell;
+        const double p0 = pq[0], p1 = pq[g.plane], p2 = sq2 * pq[2 * g.plane];
+        const double m = fmax(1.0, sqrt(2.0 * (p0 * p0 + p1 * p1 + p2 * p2)));
+        const double ts = t0 * s0 + t1 * s1 + t2 * s2;
+        const double ps = p0 * s0 + p1 * s1 + p2 * s2;
+        const double f = inv * inv / m;
+        double* pt = pi_t + (long long)(3 * q) * g.plane + cell;
+        pt[0] = (t0 + s0) * inv - (ts * p0 + ps * t0) * f;
+        pt[g.plane] = (t1 + s1) * inv - (ts * p1 + ps * t1) * f;
+        pt[2 * g.plane] = ((t2 + s2) * inv - (ts * p2 + ps * t2) * f) * (1.0 / sq2);
+      }
+      // energy and residual at u = v + dv
+      const Qp p = eval_qp(c, xi, eta);
+      double txx, tyy, txy;
+      tau_hat(ph, p, txx, tyy, txy);
+      const double tt = (txx * txx + tyy * tyy + 2.0 * txy * txy) * idx * idx;
+      const double d2 = ph.dmin2 + 2.0 * tt;
+      const double inv = rsqrt(d2);
+      const double Dl = d2 * inv;
+      const double tr = (p.gxx + p.gyy) * idx;
+      const double wx = voq[(2 * q) * g.plane + cell] - p.vx;
+      const double wy = voq[(2 * q + 1) * g.plane + cell] - p.vy;
+      const double nw = sqrt(wx * wx + wy * wy);
+      const double fx = fq[(2 * q) * g.plane + cell], fy = fq[(2 * q + 1) * g.plane + cell];
+      const double e1 = ph.w * 0.5 * rh * (p.vx * p.vx + p.vy * p.vy);
+      const double e2 = ph.w * (fx * p.vx + fy * p.vy);
+      const double e3 = ph.w * 0.5 * Pdt * (Dl - tr);
+      const double e4 = ph.w * ph.dt * ph.cdrag * nw * nw * nw * (1.0 / 3.0);
+      acc.add(e1);
+      acc.add(e2);
+      acc.add(e3);
+      acc.add(e4);
+      asum += fabs(e1) + fabs(e2) + fabs(e3) + fabs(e4);
+      const double sfac = Pdt * inv * idx;
+      const double Sxx = sfac * txx, Syy = sfac * tyy, Sxy = sfac * txy;
+      const double Fxx = ph.ta * Sxx + ph.tb * Syy - 0.5 * Pdt;
+      const double Fyy = ph.tb * Sxx + ph.ta * Syy - 0.5 * Pdt;
+      const double Fxy = 2.0 * ph.tc * Sxy;
+      const double dr = ph.dt * ph.cdrag * nw;
+      const double sx = ph.w * (rh * p.vx + fx - dr * wx);
+      const double sy = ph.w * (rh * p.vy + fy - dr * wy);
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        double n, dxi, deta;
+        shape(k, xi, eta, n, dxi, deta);
+        rx[k] += n * sx + vpw * (Fxx * dxi + Fxy * deta);
+        ry[k] += n * sy + vpw * (Fxy * dxi + Fyy * deta);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      eb[(2 * k) * g.plane + cell] = rx[k];
+      eb[(2 * k + 1) * g.plane + cell] = ry[k];
+    }
+  }
+  __shared__ double sh_hi[256], sh_lo[256];
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int nt = blockDim.x * blockDim.y;
+  sh_hi[tid] = acc.hi;
+  sh_lo[tid] = acc.lo;
+  __syncthreads();
+  for (int st = nt / 2; st > 0; st >>= 1) {
+    if (tid < st) {
+      DD x{sh_hi[tid], sh_lo[tid]};
+      x.add(DD{sh_hi[tid + st], sh_lo[tid + st]});
+      sh_hi[tid] = x.hi;
+      sh_lo[tid] = x.lo;
+    }
+    __syncthreads();
+  }
+  if (tid == 0) {
+    partial[bid] = sh_hi[0];
+    partial[nblocks + bid] = sh_lo[0];
+  }
+  asum = block_sum(asum);
+  if (tid == 0) partial[(2 * MAX_ALPHA) * nblocks + bid] = asum;
+}
+
 inline dim3 cell_grid(const Layout& g, dim3 blk) {
   return dim3((g.N + blk.x - 1) / blk.x, (g.N + blk.y - 1) / blk.y);
 }
@@ -597,13 +765,13 @@ void launch_energy(cudaStream_t s, const Layout& g, const Phys& ph, int k, const
 
 template <typename TE>
 void launch_element_matrices(cudaStream_t s, const Layout& g, const Phys& ph, const double2* v, const double* pi,
-                             const double* P, const double* rhoH, const double* voq, TE* ke, float* qcoef) {
+                             const double* P, const double* rhoH, const double* voq, TE* ke) {
   note_launch();
-  k_element_matrices<TE><<<cell_grid(g, kCellBlock), kCellBlock, 0, s>>>(g, ph, v, pi, P, rhoH, voq, ke, qcoef);
+  k_element_matrices<TE><<<cell_grid(g, kCellBlock), kCellBlock, 0, s>>>(g, ph, v, pi, P, rhoH, voq, ke);
 }
 template void launch_element_matrices<double>(cudaStream_t, const Layout&, const Phys&, const double2*,
                                               const double*, const double*, const double*, const double*,
-                                              double*, float*);
+                                              double*);
 
 template <typename TE, typename TS>
 void launch_stencil_from_elements(cudaStream_t s, const Layout& g, const TE* ke, TS* st) {
@@ -611,6 +779,19 @@ void launch_stencil_from_elements(cudaStream_t s, const Layout& g, const TE* ke,
   k_stencil_from_elements<TE, TS><<<node_grid(g, kNodeBlock), kNodeBlock, 0, s>>>(g, ke, st);
 }
 template void launch_stencil_from_elements<double, double>(cudaStream_t, const Layout&, const double*, double*);
+
+void launch_trial(cudaStream_t s, const Layout& g, const Phys& ph, const double2* v, const double2* dv,
+                  const double* P, const double* rhoH, const double* fq, const double* voq, const double* pi,
+                  double* pi_t, double* eb, double2* R, double* partial_e, double* out_e, double* partial_r) {
+  dim3 gr = cell_grid(g, kCellBlock);
+  const int nb = gr.x * gr.y;
+  note_launch();
+  k_trial_cells<<<gr, kCellBlock, 0, s>>>(g, ph, v, dv, P, rhoH, fq, voq, pi, pi_t, eb, partial_e, nb);
+  note_launch();
+  k_energy_final<<<1, 1024, 0, s>>>(1, partial_e, nb, out_e);
+  note_launch();
+  k_residual_nodes<<<node_grid(g, kNodeBlock), kNodeBlock, 0, s>>>(g, eb, R, partial_r);
+}
 
 void launch_dual_update(cudaStream_t s, const Layout& g, const Phys& ph, double alpha, const double2* v,
                         const double2* dv, double* pi) {

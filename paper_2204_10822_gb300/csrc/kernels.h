@@ -33,11 +33,17 @@ void launch_energy(cudaStream_t s, const Layout& g, const Phys& ph, int k, const
                    double* partial, double* out);
 template <typename TE>
 void launch_element_matrices(cudaStream_t s, const Layout& g, const Phys& ph, const double2* v, const double* pi,
-                             const double* P, const double* rhoH, const double* voq, TE* ke, float* qcoef);
+                             const double* P, const double* rhoH, const double* voq, TE* ke);
 template <typename TE, typename TS>
 void launch_stencil_from_elements(cudaStream_t s, const Layout& g, const TE* ke, TS* st);
 void launch_dual_update(cudaStream_t s, const Layout& g, const Phys& ph, double alpha, const double2* v,
                         const double2* dv, double* pi);
+// Fused unit-step trial at v + dv: energy -> out_e[0] (scale in out_e[MAX_ALPHA]),
+// residual -> R (norm^2 partials in partial_r, residual_partials(g) of them),
+// trial dual state -> pi_t.
+void launch_trial(cudaStream_t s, const Layout& g, const Phys& ph, const double2* v, const double2* dv,
+                  const double* P, const double* rhoH, const double* fq, const double* voq, const double* pi,
+                  double* pi_t, double* eb, double2* R, double* partial_e, double* out_e, double* partial_r);
 
 // ---- stencil / multigrid kernels (mg_kernels.cu) ----
 // y = A x on interior nodes (0 elsewhere); TA accumulates.
@@ -48,7 +54,7 @@ template <typename TS, typename TV>
 void launch_residual_stencil(cudaStream_t s, const Layout& g, const TS* st, const TV* x, const TV* b, TV* r);
 // Block-Jacobi inverse (3 planes: xx, xy, yy) and per-block Gershgorin maxima.
 template <typename TS, typename TD>
-int launch_dinv_gershgorin(cudaStream_t s, const Layout& g, const TS* st, TD* dinv, double* partial);
+int launch_dinv_gershgorin(cudaStream_t s, const Layout& g, const TS* st, TD* dinv, double* partial, bool bound);
 void launch_max_final(cudaStream_t s, const double* partial, int n, double* out);
 // lambda_max(D^-1 A) ~= safety |x_k| / |x_{k-1}| after k power steps from the
 // checkerboard vector (x0, x1: level vectors used as scratch).

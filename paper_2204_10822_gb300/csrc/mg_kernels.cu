@@ -134,7 +134,7 @@ __global__ void k_residual_stencil(Layout g, const TS* __restrict__ st, const TV
 
 template <typename TS, typename TD>
 __global__ void k_dinv_gershgorin(Layout g, const TS* __restrict__ st, TD* __restrict__ dinv,
-                                  double* __restrict__ partial) {
+                                  double* __restrict__ partial, int bound) {
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int j = blockIdx.y * blockDim.y + threadIdx.y;
   double gmax = 0.0;
@@ -149,7 +149,7 @@ __global__ void k_dinv_gershgorin(Layout g, const TS* __restrict__ st, TD* __res
       i01 = -d[1] / det;
       i11 = d[0] / det;
       double r0 = 0, r1 = 0;
-      for (int dj = -1; dj <= 1; ++dj)
+      for (int dj = -1; dj <= 1 && bound; ++dj)
         for (int di = -1; di <= 1; ++di) {
           if (!is_interior(i + di, j + dj, g.N)) continue;
           double b[4];
@@ -517,10 +517,10 @@ void launch_residual_stencil(cudaStream_t s, const Layout& g, const TS* st, cons
 }
 
 template <typename TS, typename TD>
-int launch_dinv_gershgorin(cudaStream_t s, const Layout& g, const TS* st, TD* dinv, double* partial) {
+int launch_dinv_gershgorin(cudaStream_t s, const Layout& g, const TS* st, TD* dinv, double* partial, bool bound) {
   dim3 gr = ngrid(g);
   note_launch();
-  k_dinv_gershgorin<TS, TD><<<gr, kBlk, 0, s>>>(g, st, dinv, partial);
+  k_dinv_gershgorin<TS, TD><<<gr, kBlk, 0, s>>>(g, st, dinv, partial, bound ? 1 : 0);
   return gr.x * gr.y;
 }
 
@@ -635,7 +635,7 @@ void launch_convert_stencil(cudaStream_t s, const Layout& g, const TA* a, TB* b)
 #define SVN_INST_LEVEL(TS, TD, TV)                                                                                 \
   template void launch_residual_stencil<TS, TV>(cudaStream_t, const Layout&, const TS*, const TV*, const TV*,    \
                                                 TV*);                                                            \
-  template int launch_dinv_gershgorin<TS, TD>(cudaStream_t, const Layout&, const TS*, TD*, double*);             \
+  template int launch_dinv_gershgorin<TS, TD>(cudaStream_t, const Layout&, const TS*, TD*, double*, bool);       \
   template void launch_cheb_zero_start<TS, TD, TV>(cudaStream_t, const Layout&, const TD*,                      \
                                                    const typename ScalarOf<TV>::type*, const TV*, TV*, TV*);     \
   template void launch_cheb_sweep<TS, TD, TV>(cudaStream_t, const Layout&, const TS*, const TD*,                 \
@@ -647,7 +647,8 @@ SVN_INST_LEVEL(double, double, double2)
 SVN_INST_LEVEL(__nv_bfloat16, float, float2)
 SVN_INST_LEVEL(float, float, float2)
 
-template int launch_dinv_gershgorin<double, float>(cudaStream_t, const Layout&, const double*, float*, double*);
+template int launch_dinv_gershgorin<double, float>(cudaStream_t, const Layout&, const double*, float*, double*,
+                                                   bool);
 template void launch_restrict<double2>(cudaStream_t, const Layout&, const Layout&, const double2*, double2*);
 template void launch_restrict<float2>(cudaStream_t, const Layout&, const Layout&, const float2*, float2*);
 template void launch_prolong_add<double2>(cudaStream_t, const Layout&, const Layout&, const double2*, double2*);

@@ -66,7 +66,9 @@ struct svn_handle {
 
   // Newton state
   double2 *v = nullptr, *dv = nullptr, *vt = nullptr, *R = nullptr, *rhs = nullptr;
+  double2* Rt = nullptr;        // residual at the trial point v + dv
   double* pi = nullptr;
+  double* pi_t = nullptr;       // dual state at the trial point
   double* pi_scratch = nullptr;
   bool state_set = false;
   double* eb = nullptr;         // element buffer, NELEM planes FP64
@@ -275,7 +277,7 @@ int linearize(svn_handle* h, const double2* v, const double* pi) {
   cudaStream_t s = h->stream;
   {
     Prof pr(h, SVN_K_ELEMENT);
-    launch_element_matrices<double>(s, h->g0, ph, v, pi, h->P, h->rhoH, h->voq, h->eb, nullptr);
+    launch_element_matrices<double>(s, h->g0, ph, v, pi, h->P, h->rhoH, h->voq, h->eb);
   }
   launch_stencil_from_elements<double, double>(s, h->g0, h->eb, h->lv[0].st64);
   CKL();
@@ -293,9 +295,11 @@ int linearize(svn_handle* h, const double2* v, const double* pi) {
         launch_convert_stencil<double, float>(s, lv.g, lv.st64, lv.st32);
       else
         launch_convert_stencil<double, __nv_bfloat16>(s, lv.g, lv.st64, lv.st16);
-      nb = launch_dinv_gershgorin<double, float>(s, lv.g, lv.st64, (float*)lv.dinv, h->partial);
+      nb = launch_dinv_gershgorin<double, float>(s, lv.g, lv.st64, (float*)lv.dinv, h->partial,
+                                                 h->prm.lmax_iters == 0);
     } else {
-      nb = launch_dinv_gershgorin<double, double>(s, lv.g, lv.st64, (double*)lv.dinv, h->partial);
+      nb = launch_dinv_gershgorin<double, double>(s, lv.g, lv.st64, (double*)lv.dinv, h->partial,
+                                                  h->prm.lmax_iters == 0);
     }
     launch_max_final(s, h->partial, nb, lv.lmax);
     if (h->prm.lmax_iters > 0) {
@@ -659,6 +663,8 @@ int create_impl(svn_handle* h, const svn_grid* g, const svn_params* p, void* str
   TRY(dalloc(h, &h->rhs, pl));
   TRY(dalloc(h, &h->w, pl));
   TRY(dalloc(h, &h->pi, 12 * pl));
+  TRY(dalloc(h, &h->pi_t, 12 * pl));
+  TRY(dalloc(h, &h->Rt, pl));
   TRY(dalloc(h, &h->eb, (size_t)NELEM * pl));
   const size_t vsz = h->mixed ? sizeof(float2) : sizeof(double2);
   for (size_t l = 0; l < h->lv.size(); ++l) {
@@ -686,8 +692,9 @@ int create_impl(svn_handle* h, const svn_grid* g, const svn_params* p, void* str
   TRY(dalloc(h, &h->ybuf, (size_t)h->restart + 1));
   const int nw = krylov_blocks(g0);
   h->partial_len = (size_t)std::max<long long>(
-      {(long long)nw * (h->restart + 1), (long long)residual_partials(g0), (long long)energy_partials(g0) * (2 * MAX_ALPHA + 1),
-       (long long)reduce_blocks(pl), 4096});
+      {(long long)nw * (h->restart + 1), (long long)residual_partials(g0),
+       (long long)energy_partials(g0) * (2 * MAX_ALPHA + 1) + residual_partials(g0), (long long)reduce_blocks(pl),
+       4096});
   TRY(dalloc(h, &h->partial, h->partial_len));
   TRY(dalloc(h, &h->scal, 64));
   h->hostbuf_len = 4 * (size_t)(h->restart + 2) + 64;
@@ -699,7 +706,7 @@ void destroy_impl(svn_handle* h) {
   dfree(h->in_h); dfree(h->in_A); dfree(h->in_wind); dfree(h->in_ocean); dfree(h->in_vold);
   dfree(h->P); dfree(h->rhoH); dfree(h->fq); dfree(h->voq);
   dfree(h->v); dfree(h->dv); dfree(h->vt); dfree(h->R); dfree(h->rhs); dfree(h->w);
-  dfree(h->pi); dfree(h->pi_scratch); dfree(h->eb);
+  dfree(h->pi); dfree(h->pi_t); dfree(h->Rt); dfree(h->pi_scratch); dfree(h->eb);
   for (Level& L : h->lv) {
     dfree(L.st64); dfree(L.st16); dfree(L.st32); dfree(L.dinv); dfree(L.lmax); dfree(L.cheb);
     dfree(L.x[0]); dfree(L.x[1]); dfree(L.d); dfree(L.b); dfree(L.r);
@@ -788,9 +795,16 @@ int step_impl(svn_handle* h, double dt, double tol, svn_stats* st) {
   }
   const svn_params& p = h->prm;
   double eta_prev = p.ew_eta_max;
+  bool have_r = false;      // R and its norm at v were produced by the accepted trial
+  double r_next = 0.0;
   for (int it = 0;; ++it) {
     double r;
-    TRY(residual(h, h->v, h->R, &r));
+    if (have_r) {
+      r = r_next;
+      have_r = false;
+    } else {
+      TRY(residual(h, h->v, h->R, &r));
+    }
     st->res_hist[it] = r;
     st->newton_iters = it;
     st->res_final = r;
@@ -822,10 +836,43 @@ int step_impl(svn_handle* h, double dt, double tol, svn_stats* st) {
     TRY(fgmres(h, h->rhs, h->dv, eta, p.max_krylov, &kits));
     st->krylov_per_newton[it] = kits;
     st->krylov_iters_total += kits;
-    // backtracking on Phi (Section 5.1)
+    // backtracking on Phi (Section 5.1); the unit step is tried first in one
+    // fused pass that also yields R and pi at the trial point
     double alpha = 1.0, phi1 = 0.0, scale1 = 0.0;
     bool ok = false;
-    for (int k = 0; k <= p.max_halvings; ++k) {
+    int k0 = 0;
+    if (p.fused_trial) {
+      {
+        Prof pr(h, SVN_K_ENERGY);
+        double* pr_res = h->partial + (size_t)energy_partials(g) * (2 * MAX_ALPHA + 1);
+        launch_trial(s, g, ph, h->v, h->dv, h->P, h->rhoH, h->fq, h->voq, h->pi, h->pi_t, h->eb, h->Rt,
+                     h->partial, h->scal, pr_res);
+        launch_sum_final(s, pr_res, residual_partials(g), h->scal + MAX_ALPHA + 1);
+      }
+      CKL();
+      double out[MAX_ALPHA + 2];
+      TRY(sync_read(h, h->scal, MAX_ALPHA + 2, out));
+      phi1 = out[0];
+      scale1 = out[MAX_ALPHA];
+      const double rt = std::sqrt(out[MAX_ALPHA + 1]);
+      ok = phi1 < phi0 || (std::fabs(phi1 - phi0) <= p.ls_floor * scale0 && rt < r);
+      if (ok) {
+        st->alpha_hist[it] = 1.0;
+        launch_axpy(s, g, 1.0, h->dv, h->v);
+        CKL();
+        std::swap(h->pi, h->pi_t);
+        std::swap(h->R, h->Rt);
+        r_next = rt;
+        have_r = true;
+        phi0 = phi1;
+        scale0 = scale1;
+        continue;
+      }
+      st->halvings_total += 1;
+      alpha = 0.5;
+      k0 = 1;
+    }
+    for (int k = k0; k <= p.max_halvings; ++k) {
       TRY(energy(h, h->v, h->dv, &alpha, 1, &phi1, &scale1));
       if (phi1 < phi0) {
         ok = true;
@@ -890,6 +937,7 @@ int svn_default_params(svn_params* p) {
   p->lmax_iters = 15;
   p->lmax_safety = 1.15;
   p->vcycle_fp32 = 1;
+  p->fused_trial = 1;
   return SVN_OK;
 }
 

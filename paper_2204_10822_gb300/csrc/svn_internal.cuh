@@ -25,7 +25,7 @@ namespace svn {
 constexpr int NSTEN = 19;
 enum StencilSlot { S_D = 0, S_E = 3, S_N = 7, S_NE = 11, S_NW = 15 };
 constexpr int NELEM = 36;   // unique entries of the symmetric 8x8 element matrix
-constexpr int NQCOEF = 9;   // per quadrature point: C (6, symmetric Voigt) + M (3)
+
 
 // Gauss points on [0, 1]
 constexpr double GQ0 = 0.21132486540518711775;   // 1/2 - 1/(2 sqrt 3)

@@ -54,3 +54,25 @@ def test_default_params_and_argument_checks(lib):
     assert b"even" in lib.svn_last_error(h)
     lib.svn_destroy(h)
     assert lib.svn_destroy(None) == -1
+
+
+def _struct_fields(name):
+    hdr = open(os.path.join(ROOT, "include", "svn.h")).read()
+    hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
+    body = re.search(r"typedef struct %s \{(.*?)\} %s;" % (name, name), hdr, flags=re.S).group(1)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if not decl:
+            continue
+        decl = re.sub(r"^(int|double|const\s+\w+\s*\*)\s+", "", decl)
+        for part in decl.split(","):
+            names.append(re.sub(r"\[.*\]", "", part).strip())
+    return names
+
+
+@pytest.mark.parametrize("cname,pyname", [("svn_params", "SvnParams"), ("svn_stats", "SvnStats"),
+                                          ("svn_grid", "SvnGrid")])
+def test_ctypes_structs_match_header(cname, pyname):
+    from paper_2204_10822_gb300 import capi
+    assert _struct_fields(cname) == [f[0] for f in getattr(capi, pyname)._fields_]

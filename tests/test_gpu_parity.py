@@ -172,11 +172,11 @@ def test_krylov_solve_parity():
     assert abs(its - its_o) <= 1, (its, its_o)
 
 
-@pytest.mark.parametrize("N", [16, 64])
-def test_step_parity_fp64(N):
+@pytest.mark.parametrize("N,fused", [(16, 1), (64, 1), (64, 0)])
+def test_step_parity_fp64(N, fused):
     p = W.config(0, N=N)
     res = newton(p, tol=1e-10)
-    s = make_solver(p)
+    s = make_solver(p, fused_trial=fused)
     v, stats = s.step(p.dt, 1e-10)
     v = host(v)
     err = np.linalg.norm(v - res.v) / np.linalg.norm(res.v)
