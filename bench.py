@@ -46,6 +46,9 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison step")
+    ap.add_argument("--ensemble", action="store_true",
+                    help="ensemble workload: 64 instances, N ~ U{128,256,512,1024}, one step each")
+    ap.add_argument("--ensemble-size", type=int, default=64)
     return ap.parse_args()
 
 
@@ -293,8 +296,61 @@ def run_ours(args, rank, world):
     return result
 
 
+def run_ensemble(args):
+    """64 independent instances of mixed grid sizes: concurrent batch step vs one by one."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2204_10822_gb300 import Batch, Solver
+
+    rng = np.random.Generator(np.random.PCG64(3))
+    Ns = [int(x) for x in rng.choice([128, 256, 512, 1024], size=args.ensemble_size)]
+    probs = [W.make_problem(N, seed=1000 + i) for i, N in enumerate(Ns)]
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    kw = dict(SETTINGS, precision="mixed", vcycle_fp32=1)
+    b = Batch(Ns, host_threads=16, **kw)
+    for i, p in enumerate(probs):
+        b.set_forcing(i, t(p.h), t(p.A), t(p.wind), t(p.ocean), t(p.v_old))
+    outs = [torch.zeros((N + 1, N + 1, 2), dtype=torch.float64, device="cuda") for N in Ns]
+    for _ in range(args.warmup):
+        b.step(1800.0, args.tol, outs)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        _, st = b.step(1800.0, args.tol, outs)
+    torch.cuda.synchronize()
+    t_batch = (time.perf_counter() - t0) / args.steps
+    # the same instances one after another on one stream
+    t_seq = 0.0
+    for i, p in enumerate(probs):
+        s = Solver(p.N, p.L, **kw)
+        s.set_forcing(t(p.h), t(p.A), t(p.wind), t(p.ocean), t(p.v_old))
+        s.step(1800.0, args.tol)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        s.step(1800.0, args.tol)
+        torch.cuda.synchronize()
+        t_seq += time.perf_counter() - t1
+        s.close()
+    dof = sum(2 * (N + 1) ** 2 for N in Ns)
+    return {"metric": "ensemble DOF-steps per second (64 instances, N ~ U{128..1024}, rel-res 1e-8)",
+            "value": dof / t_batch, "unit": "DOF/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t_batch * 1000.0, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64+f32", "data": "synthetic",
+            "config": {"workload": "ensemble of %d instances, N counts %s" % (
+                len(Ns), {n: Ns.count(n) for n in (128, 256, 512, 1024)}), "dof_total": dof,
+                "l2": "inputs larger than L2"},
+            "sequential_s": t_seq, "batch_s": t_batch, "speedup_vs_sequential": t_seq / t_batch,
+            "newton_iters_mean": float(np.mean([x["newton_iters"] for x in st])),
+            "krylov_iters_mean": float(np.mean([x["krylov_iters_total"] for x in st]))}
+
+
 def main():
     args = parse()
+    if args.ensemble:
+        print(json.dumps(run_ensemble(args)))
+        return 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     if args.impl == "reference":

@@ -245,6 +245,42 @@ int svn_autotune(svn_handle* h, double dt, int probe_newton, const int* degrees,
                  const double* los, int nl, double* best_ms);
 int svn_get_params(const svn_handle* h, svn_params* p);
 
+/* ---- Learned initial guess (no counterpart in the paper).  A U-Net on a
+ * G x G cell grid (G a multiple of 64): four levels with 32/64/128/256
+ * channels, two 3x3 convolutions + ReLU per level, 2x2 average pooling,
+ * nearest upsampling with skip concatenation, and a 3x3 head; BF16 weights
+ * and activations with FP32 accumulation (tensor-core implicit GEMMs for the
+ * forward and backward-data convolutions), Adam on FP32 master weights.
+ * Inputs (8 channels, block averages over N/G x N/G cells of an N-cell
+ * problem): h/2, (A - 0.9)/0.1, wind/15, ocean/0.1, v_old/0.2 (m/s); output:
+ * cell-centred velocity / 0.2, prolonged bilinearly to the nodes.
+ * Parameters are one FP32 vector: for each of the 15 convolutions in order its
+ * weights [Cout][3*ky+kx][Cin], then all biases in the same order.  All
+ * pointers of svn_net_set_sample are device pointers in the layouts above;
+ * v_target (may be NULL) needs N == G.  svn_net_train_step runs forward,
+ * loss 0.5 mean((out - target)^2), backward and (if apply_update) one Adam
+ * step on the first nb batch slots; *loss receives the loss (host).
+ * svn_attach_net makes svn_step try the network's prediction as v_0 when
+ * params.learned (or svn_set_learned) is on; it is used only if its residual
+ * is below ||R(v_old)||, else v_old (stats.learned_used / learned_fallback). */
+typedef struct svn_net svn_net;
+int svn_net_create(int G, int batch, void* cuda_stream, svn_net** out);
+int svn_net_destroy(svn_net* net);
+const char* svn_net_last_error(const svn_net* net);
+long long svn_net_num_params(const svn_net* net);
+int svn_net_set_params(svn_net* net, const float* host_params, long long n);
+int svn_net_get_params(svn_net* net, float* host_params, long long n);
+int svn_net_get_grads(svn_net* net, float* host_grads, long long n);
+int svn_net_set_sample(svn_net* net, int slot, int N, const double* hcell, const double* A,
+                       const double* wind, const double* ocean, const double* v_old,
+                       const double* v_target);
+/* Forward on slots [0, nb); out_host (may be NULL) receives nb x G x G x 16
+ * FP32 outputs (channels 0, 1 used). */
+int svn_net_forward(svn_net* net, int nb, float* out_host);
+int svn_net_train_step(svn_net* net, int nb, float lr, int apply_update, float* loss);
+int svn_attach_net(svn_handle* h, svn_net* net);
+int svn_set_learned(svn_handle* h, int on);
+
 /* ---- Instrumentation (no counterpart in the paper): CUDA-event timing of
  * one kernel class on the handle's stream, for roofline reporting. ---- */
 enum svn_kernel_class {

@@ -83,6 +83,18 @@ _SIGS = {
     "svn_batch_step": (c_int, [c_void_p, c_double, c_double, ctypes.POINTER(c_void_p), ctypes.POINTER(SvnStats)]),
     "svn_autotune": (c_int, [c_void_p, c_double, c_int, ctypes.POINTER(c_int), c_int, P_double, c_int, P_double]),
     "svn_get_params": (c_int, [c_void_p, ctypes.POINTER(SvnParams)]),
+    "svn_net_create": (c_int, [c_int, c_int, c_void_p, ctypes.POINTER(c_void_p)]),
+    "svn_net_destroy": (c_int, [c_void_p]),
+    "svn_net_last_error": (ctypes.c_char_p, [c_void_p]),
+    "svn_net_num_params": (ctypes.c_longlong, [c_void_p]),
+    "svn_net_set_params": (c_int, [c_void_p, c_void_p, ctypes.c_longlong]),
+    "svn_net_get_params": (c_int, [c_void_p, c_void_p, ctypes.c_longlong]),
+    "svn_net_get_grads": (c_int, [c_void_p, c_void_p, ctypes.c_longlong]),
+    "svn_net_set_sample": (c_int, [c_void_p, c_int, c_int] + [c_void_p] * 6),
+    "svn_net_forward": (c_int, [c_void_p, c_int, c_void_p]),
+    "svn_net_train_step": (c_int, [c_void_p, c_int, ctypes.c_float, c_int, ctypes.POINTER(ctypes.c_float)]),
+    "svn_attach_net": (c_int, [c_void_p, c_void_p]),
+    "svn_set_learned": (c_int, [c_void_p, c_int]),
     "svn_residual_noalloc": (c_int, [ctypes.POINTER(SvnGrid), ctypes.POINTER(SvnParams), c_double] +
                              [c_void_p] * 7 + [P_double, c_void_p]),
 }

@@ -119,4 +119,11 @@ void launch_lincomb(cudaStream_t s, const Layout& g, const TZ* Z, long long zstr
                     double2* x);
 int krylov_blocks(const Layout& g);
 
+// ---- learned initial guess (unet.cu) ----
+struct NetImpl;
+// Predict the node velocity of the handle's grid from the forcing (caller layouts).
+void net_predict_nodes(NetImpl* n, cudaStream_t s, const Layout& g, const double* hcell, const double* A,
+                       const double* wind, const double* ocean, const double* vold, double2* v);
+int net_grid(const NetImpl* n);
+
 }  // namespace svn

@@ -25,6 +25,8 @@
 
 using namespace svn;
 
+svn::NetImpl* svn_net_impl(svn_net* net);   // unet.cu
+
 namespace {
 
 struct Level {
@@ -85,6 +87,9 @@ struct svn_handle {
   double* scal = nullptr;       // device scalars
   double* hostbuf = nullptr;    // pinned host mirror
   size_t hostbuf_len = 0;
+
+  // learned initial guess (not owned)
+  svn::NetImpl* net = nullptr;
 
   // the V-cycle as a CUDA graph: input in lv[0].b, output in lv[0].x[1]
   cudaGraph_t vc_graph = nullptr;
@@ -784,6 +789,18 @@ int step_impl(svn_handle* h, double dt, double tol, svn_stats* st) {
   TRY(residual(h, h->vt, h->R, &st->res0));
   if (!h->state_set) {
     CK(cudaMemcpyAsync(h->v, h->vt, sizeof(double2) * g.plane, cudaMemcpyDeviceToDevice, s));
+    if (h->prm.learned && h->net && g.N % net_grid(h->net) == 0) {
+      // learned start: kept only if its residual is below that of v^n
+      st->learned_used = 1;
+      net_predict_nodes(h->net, s, g, h->in_h, h->in_A, h->in_wind, h->in_ocean, h->in_vold, h->vt);
+      CKL();
+      double rp;
+      TRY(residual(h, h->vt, h->w, &rp));
+      if (std::isfinite(rp) && rp < st->res0)
+        CK(cudaMemcpyAsync(h->v, h->vt, sizeof(double2) * g.plane, cudaMemcpyDeviceToDevice, s));
+      else
+        st->learned_fallback = 1;
+    }
     launch_pi_init(s, g, ph, h->v, h->pi);
     CKL();
   }
@@ -1270,6 +1287,18 @@ int svn_autotune(svn_handle* h, double dt, int probe_newton, const int* degrees,
   h->prm.cheb_lo = bl;
   h->graph_dirty = true;
   if (best_ms) *best_ms = best;
+  return SVN_OK;
+}
+
+int svn_attach_net(svn_handle* h, svn_net* net) {
+  if (!h) return SVN_ERR_ARG;
+  h->net = svn_net_impl(net);
+  return SVN_OK;
+}
+
+int svn_set_learned(svn_handle* h, int on) {
+  if (!h) return SVN_ERR_ARG;
+  h->prm.learned = on ? 1 : 0;
   return SVN_OK;
 }
 

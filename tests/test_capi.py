@@ -14,7 +14,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 def declared_functions():
     hdr = open(os.path.join(ROOT, "include", "svn.h")).read()
     hdr = re.sub(r"/\*.*?\*/", "", hdr, flags=re.S)
-    return sorted(set(re.findall(r"^\s*(?:int|const char\s*\*|unsigned long long|svn_handle\s*\*)\s*(svn_\w+)\s*\(", hdr,
+    return sorted(set(re.findall(r"^\s*(?:int|const char\s*\*|unsigned long long|long long|svn_handle\s*\*)\s*(svn_\w+)\s*\(", hdr,
                                  flags=re.M)))
 
 

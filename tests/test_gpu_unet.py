@@ -1,0 +1,110 @@
+"""The learned-start network on the GPU against the PyTorch CPU oracle, and
+what it gains inside the solver.
+
+Tolerances: BF16 activations and weights (8-bit mantissa) with FP32
+accumulation over up to 9 x 384 products; the forward output is compared by
+relative L2 error <= 3e-2, gradients per layer by cosine >= 0.98 and relative
+L2 error <= 1e-1 (activation gradients are also BF16).
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import unet as OU
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def smooth_v(N, seed):
+    rng = np.random.default_rng(seed)
+    x = np.linspace(0, 1, N + 1)
+    X, Y = np.meshgrid(x, x, indexing="xy")
+    v = np.stack([0.1 * np.sin(np.pi * X) * np.sin(2 * np.pi * Y) * rng.uniform(0.5, 1.5),
+                  -0.1 * np.sin(2 * np.pi * X) * np.sin(np.pi * Y) * rng.uniform(0.5, 1.5)], -1)
+    v[0], v[-1], v[:, 0], v[:, -1] = 0, 0, 0, 0
+    return v
+
+
+def test_forward_and_gradients_match_oracle():
+    from paper_2204_10822_gb300.learned import Net
+    G = 64
+    net = Net(G=G, batch=2)
+    p = OU.he_init(5)
+    p[-sum(co for _, co, _ in OU.LAYERS):] = np.random.default_rng(1).standard_normal(
+        sum(co for _, co, _ in OU.LAYERS)).astype(np.float32) * 0.05
+    net.set_params(p)
+    probs = [W.make_problem(G, seed=30 + k, v_old=smooth_v(G, k)) for k in range(2)]
+    targets = [smooth_v(G, 10 + k) for k in range(2)]
+    for k, q in enumerate(probs):
+        net.set_sample(k, G, dev(q.h), dev(q.A), dev(q.wind), dev(q.ocean), dev(q.v_old), dev(targets[k]))
+    out = net.forward(2)                                     # (2, G, G, 16)
+    X = np.stack([OU.features(G, G, q.h, q.A, q.wind, q.ocean, q.v_old) for q in probs])
+    ref = OU.forward(p.astype(np.float64), X).detach().numpy()   # (2, 16, G, G)
+    got = np.moveaxis(out, -1, 1)
+    assert np.linalg.norm(got - ref) <= 3e-2 * np.linalg.norm(ref)
+    T = np.stack([OU.target(v) for v in targets])
+    loss_gpu = net.train_step(2, 0.0, apply=False)
+    g_gpu = net.grads().astype(np.float64)
+    loss_ref, g_ref = OU.loss_and_grads(p.astype(np.float64), X, T)
+    assert abs(loss_gpu - loss_ref) <= 3e-2 * loss_ref
+    off = 0
+    for ci, co, _ in OU.LAYERS:
+        n = co * 9 * ci
+        a, b = g_gpu[off:off + n], g_ref[off:off + n]
+        cos = a @ b / (np.linalg.norm(a) * np.linalg.norm(b) + 1e-300)
+        assert cos >= 0.98 and np.linalg.norm(a - b) <= 1e-1 * np.linalg.norm(b), (ci, co, cos)
+        off += n
+
+
+def test_prediction_prolongation_matches_oracle():
+    from paper_2204_10822_gb300 import Solver
+    from paper_2204_10822_gb300.learned import Net
+    G, N = 64, 128
+    net = Net(G=G, batch=1)
+    p = OU.he_init(7)
+    net.set_params(p)
+    q = W.make_problem(N, seed=3, v_old=smooth_v(N, 2))
+    s = Solver(N, q.L, max_newton=0)
+    s.set_forcing(dev(q.h), dev(q.A), dev(q.wind), dev(q.ocean), dev(q.v_old))
+    net.attach(s)
+    _, st = s.step(q.dt, 1e-8, raise_on_error=False)   # max_newton 0: returns the chosen start
+    assert st["learned_used"] == 1
+    v0, _ = s.get_state()
+    X = OU.features(N, G, q.h, q.A, q.wind, q.ocean, q.v_old)[None]
+    Y = OU.forward(p.astype(np.float64), X).detach().numpy()[0, :2]
+    pred = OU.prolong(Y, N)
+    vo = q.v_old.copy()
+    vo[0], vo[-1], vo[:, 0], vo[:, -1] = 0, 0, 0, 0
+    exp = vo if st["learned_fallback"] else pred
+    assert np.linalg.norm(v0.cpu().numpy() - exp) <= 3e-2 * np.linalg.norm(exp)
+
+
+def test_training_reduces_loss_and_learned_start_gains():
+    """Trains on solver-generated pairs at 64 x 64 and compares Newton
+    iterations with and without the learned start on held-out steps."""
+    from paper_2204_10822_gb300 import Solver
+    from paper_2204_10822_gb300.learned import Net, generate_pairs, he_init, train
+    G = 64
+    kw = dict(precision="mixed", eisenstat_walker=1, krylov_rtol=1e-4)
+    pairs, _ = generate_pairs(G, n_traj=12, steps=4, seed0=500, **kw)
+    net = Net(G=G, batch=8)
+    net.set_params(he_init(0, net.nparam))
+    losses = train(net, pairs, epochs=40, lr=2e-3)
+    assert np.mean(losses[-5:]) < 0.5 * np.mean(losses[:5])
+    test, _ = generate_pairs(G, n_traj=3, steps=4, seed0=9000, **kw)
+    its = {True: [], False: []}
+    for on in (False, True):
+        s = Solver(G, 512e3, **kw)
+        net.attach(s, on)
+        for q in test:
+            s.set_forcing(q["h"], q["A"], q["wind"], q["ocean"], q["v_old"])
+            _, st = s.step(1800.0, 1e-8)
+            its[on].append(st["newton_iters"])
+        s.close()
+    print("newton iterations without / with learned start:", np.mean(its[False]), np.mean(its[True]))
+    assert np.mean(its[True]) <= np.mean(its[False])
