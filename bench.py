@@ -28,7 +28,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
-METRIC = "s/implicit step to rel-res 1e-8 @8.4M DOF (mixed precision)"
+METRIC = "s/implicit step to rel-res 1e-8 @8.4M DOF (mixed precision + learned start)"
 UNIT = "s/step"
 SAMPLE_N = 128        # oracle sample grid for the CPU baseline / reference arm
 
@@ -49,6 +49,9 @@ def parse():
     ap.add_argument("--ensemble", action="store_true",
                     help="ensemble workload: 64 instances, N ~ U{128,256,512,1024}, one step each")
     ap.add_argument("--ensemble-size", type=int, default=64)
+    ap.add_argument("--no-learned", action="store_true", help="skip training / using the learned initial guess")
+    ap.add_argument("--learned-traj", type=int, default=64)
+    ap.add_argument("--learned-epochs", type=int, default=25)
     return ap.parse_args()
 
 
@@ -173,7 +176,24 @@ def run_ours(args, rank, world):
     p = W.config(2, N=N)
     mixed = args.precision == "mixed"
     kw = dict(SETTINGS, precision=args.precision, vcycle_fp32=1 if mixed else 0)
+    # learned initial guess: trained here (outside the timed region) on pairs the
+    # solver generates at 256 x 256, then tried by every timed step (residual rule)
+    net, learned_info = None, None
+    if mixed and not args.no_learned and N % 256 == 0:
+        from paper_2204_10822_gb300.learned import Net, generate_pairs, he_init, train
+        tl = time.perf_counter()
+        pairs, _ = generate_pairs(256, n_traj=args.learned_traj, steps=4, seed0=10000,
+                                  **dict(SETTINGS, precision="mixed", vcycle_fp32=1))
+        net = Net(G=256, batch=8)
+        net.set_params(he_init(0, net.nparam))
+        losses = train(net, pairs, epochs=args.learned_epochs, lr=2e-3)
+        torch.cuda.synchronize()
+        learned_info = {"pairs": len(pairs), "train_steps": len(losses), "loss_first": float(np.mean(losses[:10])),
+                        "loss_last": float(np.mean(losses[-10:])), "setup_s": time.perf_counter() - tl}
+        del pairs
     s = Solver(N, p.L, **kw)
+    if net is not None:
+        net.attach(s, True)
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
     dev_in = [t(p.h), t(p.A), t(p.wind), t(p.ocean), t(p.v_old)]
     s.set_forcing(*dev_in)
@@ -291,6 +311,9 @@ def run_ours(args, rank, world):
             "alpha_hist": stats[0]["alpha_hist"],
             "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "roofline_fp64_apply": roof64,
             "kernel_share": shares, "dominant_kernel_class": dom, "e2e": e2e, "fp64_path": fp64,
+            "learned": (dict(learned_info, used=[st["learned_used"] for st in stats],
+                             fallback=[st["learned_fallback"] for st in stats],
+                             rule="kept only if ||R(v_pred)|| < ||R(v_old)||") if learned_info else None),
             "speedup_vs_fp64": (fp64["s_per_step"] / (tmax / args.steps)) if fp64 else None,
         }
     return result

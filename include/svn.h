@@ -87,7 +87,7 @@ typedef struct svn_params {
   double cheb_lo;           /* lower end of the Chebyshev interval, fraction of lmax */
   int coarse_N;             /* coarsest multigrid level has coarse_N cells per side */
   int eisenstat_walker;     /* 1: adapt krylov_rtol per Newton step (timed runs) */
-  int learned;              /* 1: try the learned initial guess (svn_learned_load) */
+  int learned;              /* 1: try the learned initial guess (svn_attach_net) */
   int use_graphs;           /* 1: run each V-cycle as one captured CUDA graph */
   int reorth_always;        /* 1: always two Gram-Schmidt passes; 0: second pass only
                                when the first cancels more than half of |w|^2 */
@@ -95,6 +95,9 @@ typedef struct svn_params {
   int lmax_iters;           /* power-method steps for lambda_max(D^-1 A) per level
                                (0: Gershgorin bound) */
   double lmax_safety;       /* the estimate is multiplied by this factor */
+  int learned_rule;         /* acceptance of the learned guess v_p: 0 (default) keep it if
+                               ||R(v_p)|| < ||R(v_old)||; 1 if Phi(v_p) < Phi(v_old);
+                               2 always */
   int fused_trial;          /* 1 (default): evaluate Phi, R and pi at the unit step in one
                                fused pass; 0: separate energy / residual / dual passes */
   int vcycle_fp32;          /* mixed precision: 1 (default) stores the V-cycle stencils

@@ -122,7 +122,7 @@ def loss_and_grads(params, X, T):
     d = out[:, :2] - torch.as_tensor(T, dtype=torch.float64)
     loss = 0.5 * (d * d).mean()
     loss.backward()
-    return float(loss), p.grad.numpy()
+    return float(loss.detach()), p.grad.numpy()
 
 
 def split_params_tensor(p):

@@ -794,9 +794,22 @@ int step_impl(svn_handle* h, double dt, double tol, svn_stats* st) {
       st->learned_used = 1;
       net_predict_nodes(h->net, s, g, h->in_h, h->in_A, h->in_wind, h->in_ocean, h->in_vold, h->vt);
       CKL();
-      double rp;
-      TRY(residual(h, h->vt, h->w, &rp));
-      if (std::isfinite(rp) && rp < st->res0)
+      bool take = false;
+      if (h->prm.learned_rule == 2) {
+        take = true;
+      } else if (h->prm.learned_rule == 1) {
+        // energy rule: keep the prediction if Phi(v_pred) < Phi(v^n)
+        const double a0 = 0.0;
+        double phi_p, phi_o;
+        TRY(energy(h, h->vt, h->vt, &a0, 1, &phi_p, nullptr));
+        TRY(energy(h, h->v, h->v, &a0, 1, &phi_o, nullptr));
+        take = std::isfinite(phi_p) && phi_p < phi_o;
+      } else {
+        double rp;
+        TRY(residual(h, h->vt, h->w, &rp));
+        take = std::isfinite(rp) && rp < st->res0;
+      }
+      if (take)
         CK(cudaMemcpyAsync(h->v, h->vt, sizeof(double2) * g.plane, cudaMemcpyDeviceToDevice, s));
       else
         st->learned_fallback = 1;
@@ -955,6 +968,7 @@ int svn_default_params(svn_params* p) {
   p->lmax_safety = 1.15;
   p->vcycle_fp32 = 1;
   p->fused_trial = 1;
+  p->learned_rule = 0;
   return SVN_OK;
 }
 
