@@ -11,8 +11,8 @@ Layouts (the same as the C-ABI):
 """
 from .fields import (Constants, Problem, gaussian_random_field, ice_fields,
                      rankine_vortex, ocean_gyre, make_problem, config,
-                     translating_centre, vortex_centre, CONFIG_NAMES)
+                     translating_centre, vortex_centre, problem_one, CONFIG_NAMES)
 
 __all__ = ["Constants", "Problem", "gaussian_random_field", "ice_fields",
            "rankine_vortex", "ocean_gyre", "make_problem", "config",
-           "translating_centre", "vortex_centre", "CONFIG_NAMES"]
+           "translating_centre", "vortex_centre", "problem_one", "CONFIG_NAMES"]

@@ -140,6 +140,28 @@ def translating_centre(L: float, seed: int, t: float, speed: float = 10.0):
     return (c0[0] + s, c0[1] + s)
 
 
+def problem_one(N: int, L: float = 512e3) -> Problem:
+    """The paper's Problem I (Section 5.2): single momentum solve from rest on
+    (0, 512 km)^2 with concentration
+        A = 1 - 0.5 exp(-800 |r|) - 0.4 exp(-90 |r1|) - 0.4 exp(-90 |r1 + 0.7|),
+        r  = 0.04 - (x/1000 km - 0.25)^2 - (y/1000 km - 0.25)^2,
+        r1 = 0.1 + (2x/1000 km)^2 - (2y/1000 km)       (linear in y as printed),
+    thickness H = 2A (evaluated at cell centres), wind (5, 5) m/s, ocean 0,
+    dt = 0.5 h, Delta_min = 2e-9, no Coriolis term."""
+    const = Constants(f_c=0.0)
+    xc = (np.arange(N) + 0.5) * (L / N)
+    X, Y = np.meshgrid(xc, xc, indexing="xy")
+    xs, ys = X / 1e6, Y / 1e6
+    r = 0.04 - (xs - 0.25) ** 2 - (ys - 0.25) ** 2
+    r1 = 0.1 + (2 * xs) ** 2 - (2 * ys)
+    A = 1.0 - 0.5 * np.exp(-800 * np.abs(r)) - 0.4 * np.exp(-90 * np.abs(r1)) - 0.4 * np.exp(-90 * np.abs(r1 + 0.7))
+    A = np.clip(A, 0.0, 1.0)
+    wind = np.zeros((N + 1, N + 1, 2))
+    wind[..., 0], wind[..., 1] = 5.0, 5.0
+    z = np.zeros((N + 1, N + 1, 2))
+    return Problem(N=N, L=L, const=const, h=2.0 * A, A=A, wind=wind, ocean=z, v_old=z.copy(), dt=1800.0)
+
+
 CONFIG_NAMES = {
     0: "svN FP64, 64x64 cells (8,450 DOF), one 1800 s step from rest",
     1: "svN FP64, 512x512 cells (526,338 DOF), 10 steps, translating vortex",
