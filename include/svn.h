@@ -98,6 +98,8 @@ typedef struct svn_params {
   int learned_rule;         /* acceptance of the learned guess v_p: 0 (default) keep it if
                                ||R(v_p)|| < ||R(v_old)||; 1 if Phi(v_p) < Phi(v_old);
                                2 always */
+  int cheb_fuse;            /* 1 (default): two Chebyshev steps per pass (shared-memory
+                               tile with a one-node ring); 0: one step per pass */
   int fused_trial;          /* 1 (default): evaluate Phi, R and pi at the unit step in one
                                fused pass; 0: separate energy / residual / dual passes */
   int vcycle_fp32;          /* mixed precision: 1 (default) stores the V-cycle stencils

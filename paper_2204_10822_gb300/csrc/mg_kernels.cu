@@ -70,6 +70,41 @@ __device__ __forceinline__ void stencil_row(const TS* __restrict__ st, long long
   bwd(S_NW, n - ld + 1);
 }
 
+// The same row product with x taken from an accessor xf(di, dj) (e.g. shared memory).
+template <typename TA, typename TS, typename XF>
+__device__ __forceinline__ void stencil_row_f(const TS* __restrict__ st, long long pl, long long n, int ld, XF xf,
+                                              TA& yx, TA& yy) {
+  const TA dxx = ldc<TA>(st + (S_D + 0) * pl + n);
+  const TA dxy = ldc<TA>(st + (S_D + 1) * pl + n);
+  const TA dyy = ldc<TA>(st + (S_D + 2) * pl + n);
+  const auto xp = xf(0, 0);
+  yx = dxx * (TA)xp.x + dxy * (TA)xp.y;
+  yy = dxy * (TA)xp.x + dyy * (TA)xp.y;
+  auto fwd = [&](int slot, int di, int dj) {
+    const auto xq = xf(di, dj);
+    const TA b0 = ldc<TA>(st + (slot + 0) * pl + n), b1 = ldc<TA>(st + (slot + 1) * pl + n);
+    const TA b2 = ldc<TA>(st + (slot + 2) * pl + n), b3 = ldc<TA>(st + (slot + 3) * pl + n);
+    yx += b0 * (TA)xq.x + b1 * (TA)xq.y;
+    yy += b2 * (TA)xq.x + b3 * (TA)xq.y;
+  };
+  auto bwd = [&](int slot, int di, int dj) {
+    const auto xq = xf(di, dj);
+    const long long q = n + (long long)dj * ld + di;
+    const TA b0 = ldc<TA>(st + (slot + 0) * pl + q), b1 = ldc<TA>(st + (slot + 1) * pl + q);
+    const TA b2 = ldc<TA>(st + (slot + 2) * pl + q), b3 = ldc<TA>(st + (slot + 3) * pl + q);
+    yx += b0 * (TA)xq.x + b2 * (TA)xq.y;
+    yy += b1 * (TA)xq.x + b3 * (TA)xq.y;
+  };
+  fwd(S_E, 1, 0);
+  fwd(S_N, 0, 1);
+  fwd(S_NE, 1, 1);
+  fwd(S_NW, -1, 1);
+  bwd(S_E, -1, 0);
+  bwd(S_N, 0, -1);
+  bwd(S_NE, -1, -1);
+  bwd(S_NW, 1, -1);
+}
+
 // Block K[p][p + (di, dj)], |di|, |dj| <= 1, as b[k][l] (row-major).
 template <typename TA, typename TS>
 __device__ __forceinline__ void get_block(const TS* __restrict__ st, long long pl, long long n, int ld, int di, int dj,
@@ -303,6 +338,76 @@ __global__ void k_cheb_sweep(Layout g, const TS* __restrict__ st, const TD* __re
   d[n] = mk2<TV>(dx, dy);
   const TV xo = xin[n];
   xout[n] = mk2<TV>(xo.x + dx, xo.y + dy);
+}
+
+// Two consecutive Chebyshev steps (step, step + 1) in one pass.  A 32 x 8 tile
+// keeps x0 on the tile plus a two-node ring, and the intermediate iterate x1
+// and direction d1 on the tile plus a one-node ring, in shared memory; the
+// stencil, D^-1, b and d0 are read once per pair of steps.  d0 -> d2 and
+// x0 -> x2 must be distinct buffers (neighbouring tiles read d0 and x0).
+template <typename TS, typename TD, typename TV>
+__global__ void __launch_bounds__(256) k_cheb_sweep2(Layout g, const TS* __restrict__ st, const TD* __restrict__ dinv,
+                                                     const typename ScalarOf<TV>::type* __restrict__ coef, int step,
+                                                     const TV* __restrict__ x0, TV* __restrict__ x2,
+                                                     const TV* __restrict__ d0, TV* __restrict__ d2,
+                                                     const TV* __restrict__ b) {
+  using T = typename ScalarOf<TV>::type;
+  constexpr int TX = 32, TY = 8;
+  __shared__ TV sx0[TY + 4][TX + 4];
+  __shared__ TV sx1[TY + 2][TX + 2];
+  __shared__ TV sd1[TY + 2][TX + 2];
+  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
+  const int tid = threadIdx.y * TX + threadIdx.x;
+  const TV zero = mk2<TV>(T(0), T(0));
+  for (int e = tid; e < (TY + 4) * (TX + 4); e += TX * TY) {
+    const int ly = e / (TX + 4), lx = e - ly * (TX + 4);
+    const int i = i0 - 2 + lx, j = j0 - 2 + ly;
+    sx0[ly][lx] = (i >= 0 && j >= 0 && i <= g.N && j <= g.N) ? x0[(long long)j * g.ld + i] : zero;
+  }
+  __syncthreads();
+  const T c1a = coef[2 * step], c2a = coef[2 * step + 1];
+  const T c1b = coef[2 * step + 2], c2b = coef[2 * step + 3];
+  for (int e = tid; e < (TY + 2) * (TX + 2); e += TX * TY) {
+    const int ly = e / (TX + 2), lx = e - ly * (TX + 2);
+    const int i = i0 - 1 + lx, j = j0 - 1 + ly;
+    TV x1 = zero, dd = zero;
+    if (is_interior(i, j, g.N)) {
+      const long long n = (long long)j * g.ld + i;
+      T ax, ay;
+      stencil_row_f<T>(st, g.plane, n, g.ld, [&](int di, int dj) { return sx0[ly + 1 + dj][lx + 1 + di]; }, ax, ay);
+      const TV bb = b[n];
+      const T rx = bb.x - ax, ry = bb.y - ay;
+      const T i00 = ldc<T>(dinv + n), i01 = ldc<T>(dinv + g.plane + n), i11 = ldc<T>(dinv + 2 * g.plane + n);
+      const TV dold = d0[n];
+      const T dx = c1a * dold.x + c2a * (i00 * rx + i01 * ry);
+      const T dy = c1a * dold.y + c2a * (i01 * rx + i11 * ry);
+      const TV xo = sx0[ly + 1][lx + 1];
+      dd = mk2<TV>(dx, dy);
+      x1 = mk2<TV>(xo.x + dx, xo.y + dy);
+    }
+    sx1[ly][lx] = x1;
+    sd1[ly][lx] = dd;
+  }
+  __syncthreads();
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int i = i0 + tx, j = j0 + ty;
+  if (i > g.N || j > g.N) return;
+  const long long n = (long long)j * g.ld + i;
+  if (!is_interior(i, j, g.N)) {
+    x2[n] = zero;
+    return;
+  }
+  T ax, ay;
+  stencil_row_f<T>(st, g.plane, n, g.ld, [&](int di, int dj) { return sx1[ty + 1 + dj][tx + 1 + di]; }, ax, ay);
+  const TV bb = b[n];
+  const T rx = bb.x - ax, ry = bb.y - ay;
+  const T i00 = ldc<T>(dinv + n), i01 = ldc<T>(dinv + g.plane + n), i11 = ldc<T>(dinv + 2 * g.plane + n);
+  const TV d1 = sd1[ty + 1][tx + 1];
+  const T dx = c1b * d1.x + c2b * (i00 * rx + i01 * ry);
+  const T dy = c1b * d1.y + c2b * (i01 * rx + i11 * ry);
+  d2[n] = mk2<TV>(dx, dy);
+  const TV x1 = sx1[ty + 1][tx + 1];
+  x2[n] = mk2<TV>(x1.x + dx, x1.y + dy);
 }
 
 __device__ __forceinline__ double pw(int d) { return d == 0 ? 1.0 : 0.5; }
@@ -584,6 +689,14 @@ void launch_cheb_sweep(cudaStream_t s, const Layout& g, const TS* st, const TD* 
   k_cheb_sweep<TS, TD, TV><<<ngrid(g), kBlk, 0, s>>>(g, st, dinv, coef, step, xin, xout, d, b);
 }
 
+template <typename TS, typename TD, typename TV>
+void launch_cheb_sweep2(cudaStream_t s, const Layout& g, const TS* st, const TD* dinv,
+                        const typename ScalarOf<TV>::type* coef, int step, const TV* x0, TV* x2, const TV* d0,
+                        TV* d2, const TV* b) {
+  note_launch();
+  k_cheb_sweep2<TS, TD, TV><<<ngrid(g), kBlk, 0, s>>>(g, st, dinv, coef, step, x0, x2, d0, d2, b);
+}
+
 template <typename TV>
 void launch_restrict(cudaStream_t s, const Layout& gf, const Layout& gc, const TV* rf, TV* bc) {
   note_launch();
@@ -641,7 +754,10 @@ void launch_convert_stencil(cudaStream_t s, const Layout& g, const TA* a, TB* b)
   template void launch_cheb_sweep<TS, TD, TV>(cudaStream_t, const Layout&, const TS*, const TD*,                 \
                                               const typename ScalarOf<TV>::type*, int, const TV*, TV*, TV*,      \
                                               const TV*);                                                        \
-  template void launch_coarse_dense<TS>(cudaStream_t, const Layout&, const TS*, double*);
+  template void launch_coarse_dense<TS>(cudaStream_t, const Layout&, const TS*, double*);                       \
+  template void launch_cheb_sweep2<TS, TD, TV>(cudaStream_t, const Layout&, const TS*, const TD*,                \
+                                               const typename ScalarOf<TV>::type*, int, const TV*, TV*,          \
+                                               const TV*, TV*, const TV*);
 
 SVN_INST_LEVEL(double, double, double2)
 SVN_INST_LEVEL(__nv_bfloat16, float, float2)

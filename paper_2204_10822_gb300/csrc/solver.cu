@@ -39,6 +39,7 @@ struct Level {
   void* cheb = nullptr;          // Chebyshev step coefficients (V-cycle scalar type)
   void* x[2] = {nullptr, nullptr};
   void* d = nullptr;
+  void* d2 = nullptr;            // second direction buffer for the fused two-step sweep
   void* b = nullptr;
   void* r = nullptr;
 };
@@ -100,6 +101,7 @@ struct svn_handle {
   bool recording = false;              // a V-cycle is being recorded
   cudaEvent_t gev[64] = {};            // event pairs around level-0 sweeps (graph nodes)
   int n_gev = 0;
+  long long sweep_steps[2] = {0, 0};   // recorded finest-level single / fused sweeps
 
   // instrumentation
   struct ProfRec {
@@ -345,8 +347,9 @@ struct SweepTimer {
   svn_handle* h;
   int idx = -1;
   Prof* pr = nullptr;
-  SweepTimer(svn_handle* hh, int level) : h(hh) {
+  SweepTimer(svn_handle* hh, int level, int steps) : h(hh) {
     if (level != 0) return;
+    h->sweep_steps[steps == 2 ? 1 : 0] += 1;
     if (h->recording) {
       if (!h->graph_events || h->n_gev + 2 > 64) return;
       idx = h->n_gev;
@@ -393,31 +396,43 @@ void vcycle(svn_handle* h, int l, const TV* b, TV* xout) {
   TV* x1 = (TV*)lv.x[1];
   TV* d = (TV*)lv.d;
   TV* r = (TV*)lv.r;
+  TV* nxt = nullptr;
   using T = typename ScalarOf<TV>::type;
   const int deg = h->prm.cheb_degree;
   const T* coef = (const T*)lv.cheb;
+  TV* dalt = (TV*)lv.d2;
+  TV* cur = x0;
+  const bool fuse = h->prm.cheb_fuse != 0;
+  // Chebyshev steps [k, kend) from cur; the result lands in `last_dst` when given
+  auto smooth = [&](int k, int kend, TV* last_dst) {
+    while (k < kend) {
+      const bool pair = fuse && k + 1 < kend;
+      const bool last = k + (pair ? 2 : 1) >= kend;
+      TV* dst = (last && last_dst && last_dst != cur) ? last_dst : (cur == x0 ? x1 : x0);
+      SweepTimer tm(h, l, pair ? 2 : 1);
+      if (pair) {
+        launch_cheb_sweep2<TS, TD, TV>(s, lv.g, st, dinv, coef, k, cur, dst, d, dalt, b);
+        std::swap(d, dalt);
+        k += 2;
+      } else {
+        launch_cheb_sweep<TS, TD, TV>(s, lv.g, st, dinv, coef, k, cur, dst, d, b);
+        k += 1;
+      }
+      cur = dst;
+    }
+  };
   // pre-smoothing from x = 0
   launch_cheb_zero_start<TS, TD, TV>(s, lv.g, dinv, coef, b, x0, d);
-  TV* cur = x0;
-  TV* nxt = x1;
-  for (int k = 1; k < deg; ++k) {
-    SweepTimer tm(h, l);
-    launch_cheb_sweep<TS, TD, TV>(s, lv.g, st, dinv, coef, k, cur, nxt, d, b);
-    std::swap(cur, nxt);
-  }
+  smooth(1, deg, nullptr);
   // coarse-grid correction
   launch_residual_stencil<TS, TV>(s, lv.g, st, cur, b, r);
   Level& lc = h->lv[l + 1];
   launch_restrict<TV>(s, lv.g, lc.g, r, (TV*)lc.b);
   vcycle<TS, TD, TV>(h, l + 1, (const TV*)lc.b, (TV*)lc.x[0]);
   launch_prolong_add<TV>(s, lv.g, lc.g, (const TV*)lc.x[0], cur);
-  // post-smoothing (same polynomial), the last sweep writing xout when it can
-  for (int k = 0; k < deg; ++k) {
-    TV* dst = (k == deg - 1 && xout != cur) ? xout : (cur == x0 ? x1 : x0);
-    SweepTimer tm(h, l);
-    launch_cheb_sweep<TS, TD, TV>(s, lv.g, st, dinv, coef, k, cur, dst, d, b);
-    cur = dst;
-  }
+  // post-smoothing (same polynomial)
+  smooth(0, deg, xout);
+  (void)nxt;
   if (cur != xout) cudaMemcpyAsync(xout, cur, sizeof(TV) * lv.g.plane, cudaMemcpyDeviceToDevice, s);
   (void)nxt;
 }
@@ -683,6 +698,7 @@ int create_impl(svn_handle* h, const svn_grid* g, const svn_params* p, void* str
     TRY(dalloc(h, (double**)&L.cheb, 2 * 16));
     for (int k = 0; k < 2; ++k) TRY(dalloc(h, (char**)&L.x[k], lp * vsz));
     TRY(dalloc(h, (char**)&L.d, lp * vsz));
+    TRY(dalloc(h, (char**)&L.d2, lp * vsz));
     TRY(dalloc(h, (char**)&L.b, lp * vsz));
     TRY(dalloc(h, (char**)&L.r, lp * vsz));
   }
@@ -714,7 +730,7 @@ void destroy_impl(svn_handle* h) {
   dfree(h->pi); dfree(h->pi_t); dfree(h->Rt); dfree(h->pi_scratch); dfree(h->eb);
   for (Level& L : h->lv) {
     dfree(L.st64); dfree(L.st16); dfree(L.st32); dfree(L.dinv); dfree(L.lmax); dfree(L.cheb);
-    dfree(L.x[0]); dfree(L.x[1]); dfree(L.d); dfree(L.b); dfree(L.r);
+    dfree(L.x[0]); dfree(L.x[1]); dfree(L.d); dfree(L.d2); dfree(L.b); dfree(L.r);
   }
   dfree(h->dense); dfree(h->dense_inv); dfree(h->info);
   if (h->vc_exec) cudaGraphExecDestroy(h->vc_exec);
@@ -969,6 +985,7 @@ int svn_default_params(svn_params* p) {
   p->vcycle_fp32 = 1;
   p->fused_trial = 1;
   p->learned_rule = 0;
+  p->cheb_fuse = 1;
   return SVN_OK;
 }
 

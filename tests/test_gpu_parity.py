@@ -142,16 +142,16 @@ def test_vcycle_parity_fp64():
     N = 64
     p = W.make_problem(N, seed=5)
     st = Step(p)
-    for iters in (0, 15):       # Gershgorin bound, power-method estimate
-        s = make_solver(p, coarse_N=8, cheb_degree=3, cheb_lo=0.1, lmax_iters=iters)
+    for iters, fuse, deg in ((0, 0, 3), (15, 0, 3), (15, 1, 3), (15, 1, 4)):   # bound, fusion, degree
+        s = make_solver(p, coarse_N=8, cheb_degree=deg, cheb_lo=0.1, lmax_iters=iters, cheb_fuse=fuse)
         v = rand_v(N, 5)
         pi = st.pi_of(v)
         s.linearize(p.dt, dev(v), dev(pi))
         levels = mg.build_hierarchy(st.svn_matrix(v, pi), N, coarse_N=8, power_iters=iters)
         r = rand_v(N, 6, 1.0)
         z = host(s.precondition(dev(r)))
-        zo = st.from_free(mg.vcycle(levels, st.to_free(r), degree=3, lo=0.1))
-        assert relmax(z, zo) < 1e-9, iters
+        zo = st.from_free(mg.vcycle(levels, st.to_free(r), degree=deg, lo=0.1))
+        assert relmax(z, zo) < 1e-9, (iters, fuse, deg)
 
 
 def test_krylov_solve_parity():
