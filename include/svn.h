@@ -98,6 +98,9 @@ typedef struct svn_params {
   int learned_rule;         /* acceptance of the learned guess v_p: 0 (default) keep it if
                                ||R(v_p)|| < ||R(v_old)||; 1 if Phi(v_p) < Phi(v_old);
                                2 always */
+  int mg_rebuild;           /* rebuild the V-cycle hierarchy (Galerkin levels, smoother
+                               data) every mg_rebuild Newton iterations (1 = always);
+                               the FP64 outer operator is rebuilt every iteration */
   int cheb_fuse;            /* 1 (default): two Chebyshev steps per pass (shared-memory
                                tile with a one-node ring); 0: one step per pass */
   int fused_trial;          /* 1 (default): evaluate Phi, R and pi at the unit step in one
@@ -290,7 +293,8 @@ int svn_set_learned(svn_handle* h, int on);
  * one kernel class on the handle's stream, for roofline reporting. ---- */
 enum svn_kernel_class {
   SVN_K_APPLY = 0,     /* FP64 outer Jacobian apply (stencil form) */
-  SVN_K_CHEB = 1,      /* Chebyshev-Jacobi smoothing sweeps on the finest level */
+  SVN_K_CHEB = 1,      /* finest-level Chebyshev-Jacobi sweeps (only the fused
+                          two-step launches when cheb_fuse is on) */
   SVN_K_MULTIDOT = 2,  /* FGMRES multi-dot (Arnoldi projections) */
   SVN_K_UPDATE = 3,    /* FGMRES update + norm */
   SVN_K_ELEMENT = 4,   /* element matrices of the linearisation */

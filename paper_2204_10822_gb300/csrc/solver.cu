@@ -279,7 +279,7 @@ int energy(svn_handle* h, const double2* v, const double2* dv, const double* alp
   return SVN_OK;
 }
 
-int linearize(svn_handle* h, const double2* v, const double* pi) {
+int linearize(svn_handle* h, const double2* v, const double* pi, bool hierarchy = true) {
   const Phys ph = make_phys(h, h->g0, h->cur_dt);
   cudaStream_t s = h->stream;
   {
@@ -288,6 +288,7 @@ int linearize(svn_handle* h, const double2* v, const double* pi) {
   }
   launch_stencil_from_elements<double, double>(s, h->g0, h->eb, h->lv[0].st64);
   CKL();
+  if (!hierarchy) return SVN_OK;   // the V-cycle keeps its previous hierarchy
   const int L = (int)h->lv.size();
   for (int l = 1; l < L; ++l) {
     Prof pr(h, SVN_K_RAP);
@@ -350,6 +351,8 @@ struct SweepTimer {
   SweepTimer(svn_handle* hh, int level, int steps) : h(hh) {
     if (level != 0) return;
     h->sweep_steps[steps == 2 ? 1 : 0] += 1;
+    // with fusion on, only the fused two-step launches are timed (one kernel)
+    if (h->prm.cheb_fuse && steps != 2) return;
     if (h->recording) {
       if (!h->graph_events || h->n_gev + 2 > 64) return;
       idx = h->n_gev;
@@ -557,7 +560,7 @@ int fgmres(svn_handle* h, const double2* b, double2* x, double rtol, int maxit, 
           Prof pr(h, SVN_K_MULTIDOT);
           launch_multidot(s, g, h->V, vs, j + 1, h->w, h->partial, nw);
         }
-        launch_multidot_final(s, h->partial, nw, j + 1, hp, 0);
+        launch_multidot_final(s, h->partial, j + 1 <= 32 ? multidot_blocks() : nw, j + 1, hp, 0);
         {
           Prof pr(h, SVN_K_UPDATE);
           launch_update_norm(s, g, h->V, vs, j + 1, hp, h->w, h->partial, nw);
@@ -860,7 +863,8 @@ int step_impl(svn_handle* h, double dt, double tol, svn_stats* st) {
     if (it >= p.max_newton)
       return fail(h, SVN_ERR_NO_CONVERGENCE, "no convergence in %d Newton iterations (rel-res %.3e)", it,
                   st->rel_res_final);
-    TRY(linearize(h, h->v, h->pi));
+    const int every = std::max(1, p.mg_rebuild);
+    TRY(linearize(h, h->v, h->pi, it % every == 0));
     launch_neg_copy(s, g, h->R, h->rhs);
     CKL();
     int kits = 0;
@@ -986,6 +990,7 @@ int svn_default_params(svn_params* p) {
   p->fused_trial = 1;
   p->learned_rule = 0;
   p->cheb_fuse = 1;
+  p->mg_rebuild = 1;
   return SVN_OK;
 }
 
