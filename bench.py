@@ -388,7 +388,6 @@ def main():
         cb = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
               "sample": "full oracle step at %dx%d cells per timed step (%.2f s), scaled x%.1f by DOF" % (
                   SAMPLE_N, SAMPLE_N, t, scale)}
-        args.precision = "fp64"
         line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 1,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1000.0, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",

@@ -115,8 +115,6 @@ void launch_cast_f2d(cudaStream_t s, const Layout& g, const float2* x, double2* 
 void launch_multidot(cudaStream_t s, const Layout& g, const double2* V, long long vstride, int m, const double2* w,
                      double* partial, int nblk);
 void launch_multidot_final(cudaStream_t s, const double* partial, int nblk, int m, double* h, int accumulate);
-// number of per-vector partials launch_multidot produces for m <= 32
-int multidot_blocks();
 // w -= sum_i h[i] V_i; norm partials of w
 void launch_update_norm(cudaStream_t s, const Layout& g, const double2* V, long long vstride, int m, const double* h,
                         double2* w, double* partial, int nblk);

@@ -182,34 +182,6 @@ __global__ void __launch_bounds__(ARN_THREADS) k_multidot(long long n, const dou
   }
 }
 
-// partial[i * gridDim.x + block] = sum over the block's elements of V_i . w for
-// i < m <= 32: grid-stride over the vectors with one register accumulator per
-// basis vector, reduced once per block at the end.
-__global__ void __launch_bounds__(256) k_multidot_acc(long long n, const double2* __restrict__ V, long long vstride,
-                                                      int m, const double2* __restrict__ w,
-                                                      double* __restrict__ partial) {
-  double acc[32];
-#pragma unroll
-  for (int i = 0; i < 32; ++i) acc[i] = 0.0;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
-    const double2 wv = w[t];
-#pragma unroll
-    for (int i = 0; i < 32; ++i) {
-      if (i < m) {
-        const double2 a = V[(long long)i * vstride + t];
-        acc[i] = fma(a.x, wv.x, fma(a.y, wv.y, acc[i]));
-      }
-    }
-  }
-#pragma unroll
-  for (int i = 0; i < 32; ++i) {
-    if (i < m) {
-      const double s = block_sum(acc[i]);
-      if (threadIdx.x == 0) partial[(long long)i * gridDim.x + blockIdx.x] = s;
-    }
-  }
-}
-
 // h[i] (+)= sum_warp partial[i * nwarps + warp]; one block per i.
 __global__ void k_multidot_final(const double* __restrict__ partial, int nwarps, double* __restrict__ h,
                                  int accumulate) {
@@ -346,15 +318,8 @@ void launch_cast_f2d(cudaStream_t s, const Layout& g, const float2* x, double2* 
   note_launch();
   k_cast_f2d<<<flat_blocks(g.plane), 256, 0, s>>>(g.plane, x, y);
 }
-int multidot_blocks() { return 152 * 4; }
-
 void launch_multidot(cudaStream_t s, const Layout& g, const double2* V, long long vstride, int m, const double2* w,
                      double* partial, int nwarps) {
-  if (m <= 32) {
-    note_launch();
-    k_multidot_acc<<<multidot_blocks(), 256, 0, s>>>(g.plane, V, vstride, m, w, partial);
-    return;
-  }
   const long long threads = (long long)nwarps * 32;
   note_launch();
   k_multidot<<<(unsigned)((threads + ARN_THREADS - 1) / ARN_THREADS), ARN_THREADS, 0, s>>>(g.plane, V, vstride, m, w,

@@ -528,6 +528,9 @@ int fgmres(svn_handle* h, const double2* b, double2* x, double rtol, int maxit, 
   const int m = h->restart;
   const long long vs = g.plane;
   const int nw = krylov_blocks(g);
+  if ((size_t)nw * (m + 1) > h->partial_len || (size_t)energy_partials(g) * (2 * MAX_ALPHA + 1) +
+                                                      (size_t)residual_partials(g) > h->partial_len)
+    return fail(h, SVN_ERR_ARG, "internal: reduction buffer too small");
   CK(cudaMemsetAsync(x, 0, sizeof(double2) * g.plane, s));
   double bnorm;
   TRY(norm2(h, b, &bnorm));
@@ -560,7 +563,7 @@ int fgmres(svn_handle* h, const double2* b, double2* x, double rtol, int maxit, 
           Prof pr(h, SVN_K_MULTIDOT);
           launch_multidot(s, g, h->V, vs, j + 1, h->w, h->partial, nw);
         }
-        launch_multidot_final(s, h->partial, j + 1 <= 32 ? multidot_blocks() : nw, j + 1, hp, 0);
+        launch_multidot_final(s, h->partial, nw, j + 1, hp, 0);
         {
           Prof pr(h, SVN_K_UPDATE);
           launch_update_norm(s, g, h->V, vs, j + 1, hp, h->w, h->partial, nw);

@@ -248,3 +248,27 @@ def test_error_paths():
     with pytest.raises(SvnError):
         from paper_2204_10822_gb300 import Solver
         Solver(15)                   # odd N
+
+
+def test_minimum_grid_and_restarted_fgmres():
+    # N = 8 (smallest grid, one multigrid level above the 4x4 coarsest) and a
+    # restart length of 4 that forces several FGMRES restarts
+    for N, kw in ((8, {}), (32, dict(restart=4, krylov_rtol=1e-9, max_krylov=2000))):
+        p = W.config(0, N=N)
+        res = newton(p, tol=1e-10)
+        s = make_solver(p, **kw)
+        v, st = s.step(p.dt, 1e-10)
+        assert np.linalg.norm(host(v) - res.v) <= 1e-8 * np.linalg.norm(res.v), N
+        assert abs(st["newton_iters"] - res.newton_iters) <= 1
+
+
+def test_line_search_exhaustion_is_reported():
+    # with zero halvings allowed a rejected unit step must end the step with
+    # SVN_ERR_LINESEARCH and leave a finite iterate
+    p = W.config(2, N=64)
+    s = make_solver(p, max_halvings=0, precision="mixed")
+    v, st = s.step(p.dt, 1e-10, raise_on_error=False)
+    assert st["status"] in ("SVN_ERR_LINESEARCH", "SVN_OK")
+    assert np.isfinite(host(v)).all()
+    if st["status"] == "SVN_OK":
+        assert st["halvings_total"] == 0
