@@ -14,7 +14,7 @@ unsigned long long launches_issued() { return g_launches.load(std::memory_order_
 
 namespace {
 
-constexpr int EPT = 4;              // double2 elements per thread in Arnoldi kernels
+constexpr int EPT = 8;              // double2 elements per thread in Arnoldi kernels
 constexpr int ARN_THREADS = 256;
 
 __global__ void k_sum_final(const double* __restrict__ partial, int n, double* __restrict__ out) {
