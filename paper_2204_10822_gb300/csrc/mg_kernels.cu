@@ -410,103 +410,6 @@ __global__ void __launch_bounds__(256) k_cheb_sweep2(Layout g, const TS* __restr
   x2[n] = mk2<TV>(x1.x + dx, x1.y + dy);
 }
 
-// FP32 variant of k_cheb_sweep2 that also stages the 19 stencil planes of the
-// tile plus a two-node ring in shared memory (33 KB), loaded once in a
-// coalesced burst; both steps then read coefficients from shared memory.
-template <typename TS, typename TD>
-__global__ void __launch_bounds__(256) k_cheb_sweep2_smem(Layout g, const TS* __restrict__ st,
-                                                          const TD* __restrict__ dinv, const float* __restrict__ coef,
-                                                          int step, const float2* __restrict__ x0,
-                                                          float2* __restrict__ x2, const float2* __restrict__ d0,
-                                                          float2* __restrict__ d2, const float2* __restrict__ b) {
-  constexpr int TX = 32, TY = 8, RX = TX + 4, RY = TY + 4;
-  __shared__ float sc[NSTEN][RY][RX];
-  __shared__ float2 sx0[RY][RX];
-  __shared__ float2 sx1[TY + 2][TX + 2];
-  __shared__ float2 sd1[TY + 2][TX + 2];
-  const int i0 = blockIdx.x * TX, j0 = blockIdx.y * TY;
-  const int tid = threadIdx.y * TX + threadIdx.x;
-  const long long pl = g.plane;
-  for (int e = tid; e < RY * RX; e += TX * TY) {
-    const int ly = e / RX, lx = e - ly * RX;
-    const int i = i0 - 2 + lx, j = j0 - 2 + ly;
-    const bool in = i >= 0 && j >= 0 && i <= g.N && j <= g.N;
-    const long long n = (long long)j * g.ld + i;
-    sx0[ly][lx] = in ? x0[n] : make_float2(0.f, 0.f);
-#pragma unroll
-    for (int c = 0; c < NSTEN; ++c) sc[c][ly][lx] = in ? ldc<float>(st + c * pl + n) : 0.f;
-  }
-  __syncthreads();
-  // y = A x at ring-2 coordinates (ly, lx) with x from an accessor
-  auto row = [&](int ly, int lx, auto xf, float& yx, float& yy) {
-    const float2 xp = xf(0, 0);
-    yx = sc[S_D][ly][lx] * xp.x + sc[S_D + 1][ly][lx] * xp.y;
-    yy = sc[S_D + 1][ly][lx] * xp.x + sc[S_D + 2][ly][lx] * xp.y;
-    auto fwd = [&](int slot, int di, int dj) {
-      const float2 xq = xf(di, dj);
-      yx += sc[slot][ly][lx] * xq.x + sc[slot + 1][ly][lx] * xq.y;
-      yy += sc[slot + 2][ly][lx] * xq.x + sc[slot + 3][ly][lx] * xq.y;
-    };
-    auto bwd = [&](int slot, int di, int dj) {
-      const float2 xq = xf(di, dj);
-      const int qy = ly + dj, qx = lx + di;
-      yx += sc[slot][qy][qx] * xq.x + sc[slot + 2][qy][qx] * xq.y;
-      yy += sc[slot + 1][qy][qx] * xq.x + sc[slot + 3][qy][qx] * xq.y;
-    };
-    fwd(S_E, 1, 0);
-    fwd(S_N, 0, 1);
-    fwd(S_NE, 1, 1);
-    fwd(S_NW, -1, 1);
-    bwd(S_E, -1, 0);
-    bwd(S_N, 0, -1);
-    bwd(S_NE, -1, -1);
-    bwd(S_NW, 1, -1);
-  };
-  const float c1a = coef[2 * step], c2a = coef[2 * step + 1];
-  const float c1b = coef[2 * step + 2], c2b = coef[2 * step + 3];
-  for (int e = tid; e < (TY + 2) * (TX + 2); e += TX * TY) {
-    const int ly = e / (TX + 2), lx = e - ly * (TX + 2);
-    const int i = i0 - 1 + lx, j = j0 - 1 + ly;
-    float2 x1 = make_float2(0.f, 0.f), dd = x1;
-    if (is_interior(i, j, g.N)) {
-      const long long n = (long long)j * g.ld + i;
-      float ax, ay;
-      row(ly + 1, lx + 1, [&](int di, int dj) { return sx0[ly + 1 + dj][lx + 1 + di]; }, ax, ay);
-      const float2 bb = b[n];
-      const float rx = bb.x - ax, ry = bb.y - ay;
-      const float i00 = ldc<float>(dinv + n), i01 = ldc<float>(dinv + pl + n), i11 = ldc<float>(dinv + 2 * pl + n);
-      const float2 dold = d0[n];
-      const float dx = c1a * dold.x + c2a * (i00 * rx + i01 * ry);
-      const float dy = c1a * dold.y + c2a * (i01 * rx + i11 * ry);
-      const float2 xo = sx0[ly + 1][lx + 1];
-      dd = make_float2(dx, dy);
-      x1 = make_float2(xo.x + dx, xo.y + dy);
-    }
-    sx1[ly][lx] = x1;
-    sd1[ly][lx] = dd;
-  }
-  __syncthreads();
-  const int tx = threadIdx.x, ty = threadIdx.y;
-  const int i = i0 + tx, j = j0 + ty;
-  if (i > g.N || j > g.N) return;
-  const long long n = (long long)j * g.ld + i;
-  if (!is_interior(i, j, g.N)) {
-    x2[n] = make_float2(0.f, 0.f);
-    return;
-  }
-  float ax, ay;
-  row(ty + 2, tx + 2, [&](int di, int dj) { return sx1[ty + 1 + dj][tx + 1 + di]; }, ax, ay);
-  const float2 bb = b[n];
-  const float rx = bb.x - ax, ry = bb.y - ay;
-  const float i00 = ldc<float>(dinv + n), i01 = ldc<float>(dinv + pl + n), i11 = ldc<float>(dinv + 2 * pl + n);
-  const float2 d1 = sd1[ty + 1][tx + 1];
-  const float dx = c1b * d1.x + c2b * (i00 * rx + i01 * ry);
-  const float dy = c1b * d1.y + c2b * (i01 * rx + i11 * ry);
-  d2[n] = make_float2(dx, dy);
-  const float2 x1 = sx1[ty + 1][tx + 1];
-  x2[n] = make_float2(x1.x + dx, x1.y + dy);
-}
-
 __device__ __forceinline__ double pw(int d) { return d == 0 ? 1.0 : 0.5; }
 
 template <typename TV>
@@ -791,11 +694,7 @@ void launch_cheb_sweep2(cudaStream_t s, const Layout& g, const TS* st, const TD*
                         const typename ScalarOf<TV>::type* coef, int step, const TV* x0, TV* x2, const TV* d0,
                         TV* d2, const TV* b) {
   note_launch();
-  if constexpr (std::is_same<TV, float2>::value) {
-    k_cheb_sweep2_smem<TS, TD><<<ngrid(g), kBlk, 0, s>>>(g, st, dinv, coef, step, x0, x2, d0, d2, b);
-  } else {
-    k_cheb_sweep2<TS, TD, TV><<<ngrid(g), kBlk, 0, s>>>(g, st, dinv, coef, step, x0, x2, d0, d2, b);
-  }
+  k_cheb_sweep2<TS, TD, TV><<<ngrid(g), kBlk, 0, s>>>(g, st, dinv, coef, step, x0, x2, d0, d2, b);
 }
 
 template <typename TV>
