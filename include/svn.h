@@ -98,6 +98,10 @@ typedef struct svn_params {
   int learned_rule;         /* acceptance of the learned guess v_p: 0 (default) keep it if
                                ||R(v_p)|| < ||R(v_old)||; 1 if Phi(v_p) < Phi(v_old);
                                2 always */
+  int method;               /* 0 (default): stress-velocity Newton (Section 4.2);
+                               1: standard Newton (Section 4.1, Eq. "standardNewton"),
+                               i.e. the same operator with pi = tau(v)/Delta(v) at
+                               every iteration and no dual update */
   int mg_rebuild;           /* rebuild the V-cycle hierarchy (Galerkin levels, smoother
                                data) every mg_rebuild Newton iterations (1 = always);
                                the FP64 outer operator is rebuilt every iteration */

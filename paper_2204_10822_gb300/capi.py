@@ -32,7 +32,7 @@ class SvnParams(ctypes.Structure):
         ("cheb_degree", c_int), ("cheb_lo", c_double), ("coarse_N", c_int), ("eisenstat_walker", c_int),
         ("learned", c_int), ("use_graphs", c_int), ("reorth_always", c_int),
         ("ew_eta_max", c_double), ("lmax_iters", c_int), ("lmax_safety", c_double),
-        ("learned_rule", c_int), ("mg_rebuild", c_int), ("cheb_fuse", c_int),
+        ("learned_rule", c_int), ("method", c_int), ("mg_rebuild", c_int), ("cheb_fuse", c_int),
         ("fused_trial", c_int),
         ("vcycle_fp32", c_int)]
 

@@ -644,6 +644,7 @@ int check_params(svn_handle* h, const svn_params* p) {
   if (p->precision != SVN_FP64 && p->precision != SVN_MIXED) return fail(h, SVN_ERR_ARG, "unknown precision");
   if (p->coarse_N < 2 || p->coarse_N > 16) return fail(h, SVN_ERR_ARG, "coarse_N must be in [2, 16]");
   if (p->lmax_iters < 0 || p->lmax_iters > 60) return fail(h, SVN_ERR_ARG, "lmax_iters must be in [0, 60]");
+  if (p->method != 0 && p->method != 1) return fail(h, SVN_ERR_ARG, "method must be 0 (svN) or 1 (stdN)");
   if (!(p->lmax_safety >= 1.0 && p->lmax_safety < 4.0)) return fail(h, SVN_ERR_ARG, "lmax_safety must be in [1, 4)");
   return SVN_OK;
 }
@@ -866,6 +867,12 @@ int step_impl(svn_handle* h, double dt, double tol, svn_stats* st) {
     if (it >= p.max_newton)
       return fail(h, SVN_ERR_NO_CONVERGENCE, "no convergence in %d Newton iterations (rel-res %.3e)", it,
                   st->rel_res_final);
+    if (p.method == 1) {
+      // standard Newton (Section 4.1): its Jacobian is the svN operator at
+      // pi = tau(v)/Delta(v) (where the modification is inactive)
+      launch_pi_init(s, g, ph, h->v, h->pi);
+      CKL();
+    }
     const int every = std::max(1, p.mg_rebuild);
     TRY(linearize(h, h->v, h->pi, it % every == 0));
     launch_neg_copy(s, g, h->R, h->rhs);
@@ -894,7 +901,7 @@ int step_impl(svn_handle* h, double dt, double tol, svn_stats* st) {
     double alpha = 1.0, phi1 = 0.0, scale1 = 0.0;
     bool ok = false;
     int k0 = 0;
-    if (p.fused_trial) {
+    if (p.fused_trial && p.method == 0) {
       {
         Prof pr(h, SVN_K_ENERGY);
         double* pr_res = h->partial + (size_t)energy_partials(g) * (2 * MAX_ALPHA + 1);
@@ -942,7 +949,7 @@ int step_impl(svn_handle* h, double dt, double tol, svn_stats* st) {
     }
     if (!ok) return fail(h, SVN_ERR_LINESEARCH, "line search failed after %d halvings", p.max_halvings);
     st->alpha_hist[it] = alpha;
-    {
+    if (p.method == 0) {
       Prof pr(h, SVN_K_DUAL);
       launch_dual_update(s, g, ph, alpha, h->v, h->dv, h->pi);
     }
@@ -994,6 +1001,7 @@ int svn_default_params(svn_params* p) {
   p->learned_rule = 0;
   p->cheb_fuse = 1;
   p->mg_rebuild = 1;
+  p->method = 0;
   return SVN_OK;
 }
 

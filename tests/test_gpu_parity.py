@@ -272,3 +272,25 @@ def test_line_search_exhaustion_is_reported():
     assert np.isfinite(host(v)).all()
     if st["status"] == "SVN_OK":
         assert st["halvings_total"] == 0
+
+
+def test_standard_newton_matches_oracle_stdn():
+    # stdN (Section 4.1) on the GPU against the oracle's stdN.  Its damped phase
+    # is chaotic: in the oracle itself, perturbing every Newton direction by a
+    # relative 1e-12 moves the count from 59 to 62-63, because a line-search
+    # halving decision flips after about 15 iterations.  So the first 10 step
+    # lengths must agree exactly and the residuals along them closely; then
+    # the converged solution (unique) and a count band, well above svN's
+    # (Section 5.2).
+    p = W.config(0, N=32)
+    ref = newton(p, tol=1e-10, method="stdn", max_newton=200)
+    assert ref.converged
+    s = make_solver(p, method=1, krylov_rtol=1e-11, max_krylov=2000)
+    v, st = s.step(p.dt, 1e-10, raise_on_error=False)
+    assert st["status"] == "SVN_OK"
+    k = 10
+    assert st["alpha_hist"][:k] == ref.alphas[:k], (st["alpha_hist"][:k], ref.alphas[:k])
+    np.testing.assert_allclose(st["res_hist"][:k + 1], ref.res_hist[:k + 1], rtol=1e-6)
+    assert np.linalg.norm(host(v) - ref.v) <= 1e-8 * np.linalg.norm(ref.v)
+    svn = newton(p, tol=1e-10)
+    assert 3 * svn.newton_iters <= st["newton_iters"] <= 2 * ref.newton_iters, (st["newton_iters"], ref.newton_iters)
