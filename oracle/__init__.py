@@ -22,6 +22,9 @@ sea ice"):
                    Galerkin coarse operators, block-Jacobi Chebyshev
                    smoothing, dense coarse solve, V-cycle and FGMRES, each in
                    its textbook form.
+  * ``transport`` -- explicit first-order upwind finite-volume transport of
+                   the cell fields A and H (Eqs. "model:A", "model:H",
+                   Sections 3 and 5.1), sub-cycled for the Courant number.
   * ``unet``    -- forward/backward of the small convolutional network that
                    predicts the Newton initial guess (no counterpart in the
                    paper), in plain PyTorch CPU ops.

@@ -11,8 +11,10 @@ Layouts (the same as the C-ABI):
 """
 from .fields import (Constants, Problem, gaussian_random_field, ice_fields,
                      rankine_vortex, ocean_gyre, make_problem, config,
-                     translating_centre, vortex_centre, problem_one, CONFIG_NAMES)
+                     translating_centre, vortex_centre, problem_one, problem_two,
+                     problem_two_wind, problem_two_ocean, CONFIG_NAMES)
 
 __all__ = ["Constants", "Problem", "gaussian_random_field", "ice_fields",
            "rankine_vortex", "ocean_gyre", "make_problem", "config",
-           "translating_centre", "vortex_centre", "problem_one", "CONFIG_NAMES"]
+           "translating_centre", "vortex_centre", "problem_one", "problem_two",
+           "problem_two_wind", "problem_two_ocean", "CONFIG_NAMES"]

@@ -162,6 +162,57 @@ def problem_one(N: int, L: float = 512e3) -> Problem:
     return Problem(N=N, L=L, const=const, h=2.0 * A, A=A, wind=wind, ocean=z, v_old=z.copy(), dt=1800.0)
 
 
+def problem_two_wind(N: int, t: float, L: float = 512e3) -> np.ndarray:
+    """Wind of the paper's Problem II (Section 5.3) at time t [s]: a cyclone
+    moving along the diagonal, out for 4 days and back for 4,
+        v_a = omega v_max(t) R(alpha) (x - m(t)),
+        omega = exp(-|x - m| / 100 km) / 50,
+        v_max = -15 tanh((4 - t)(4 + t) / 2) m/s (t <= 4 d),
+                 15 tanh((12 - t)(t - 4) / 2) m/s (t > 4 d),
+        alpha = 72 (t <= 4 d) or 81 degrees, R(alpha) = [[c, s], [-s, c]],
+        m_x = m_y = 256 km + 51.2 km/d t (t <= 4 d), 665.6 km - 51.2 km/d t,
+    with t in days and x - m in km (so that |v_a| peaks at 15*100/(50 e)
+    = 11 m/s at 100 km from the centre)."""
+    td = t / 86400.0
+    if td <= 4.0:
+        vmax, alpha, m = -15.0 * math.tanh((4.0 - td) * (4.0 + td) / 2.0), math.radians(72.0), 256.0 + 51.2 * td
+    else:
+        vmax, alpha, m = 15.0 * math.tanh((12.0 - td) * (td - 4.0) / 2.0), math.radians(81.0), 665.6 - 51.2 * td
+    X, Y = node_coords(N, L)
+    dx_, dy_ = X / 1e3 - m, Y / 1e3 - m
+    om = np.exp(-np.sqrt(dx_ * dx_ + dy_ * dy_) / 100.0) / 50.0
+    c, s = math.cos(alpha), math.sin(alpha)
+    w = np.empty((N + 1, N + 1, 2))
+    w[..., 0] = om * vmax * (c * dx_ + s * dy_)
+    w[..., 1] = om * vmax * (-s * dx_ + c * dy_)
+    return w
+
+
+def problem_two_ocean(N: int, L: float = 512e3) -> np.ndarray:
+    """Ocean current of Problem II: 0.01 m/s (-1 + 2y/L, 1 - 2x/L)."""
+    X, Y = node_coords(N, L)
+    o = np.empty((N + 1, N + 1, 2))
+    o[..., 0] = 0.01 * (-1.0 + 2.0 * Y / L)
+    o[..., 1] = 0.01 * (1.0 - 2.0 * X / L)
+    return o
+
+
+def problem_two(N: int, L: float = 512e3, delta_min: float = 2e-9) -> Problem:
+    """First momentum step of the paper's Problem II (Section 5.3): ice at
+    rest, A = 1, H = 0.3 m + 0.005 m (sin(60 x / 1000 km) + sin(30 y / 1000 km))
+    at cell centres, dt = 0.5 h, no Coriolis term, wind at t_1 = dt.
+    Later steps change only the wind (``problem_two_wind``), v_old, and the
+    transported A and H."""
+    const = Constants(f_c=0.0, delta_min=delta_min)
+    xc = (np.arange(N) + 0.5) * (L / N)
+    X, Y = np.meshgrid(xc, xc, indexing="xy")
+    H = 0.3 + 0.005 * (np.sin(60.0 * X / 1e6) + np.sin(30.0 * Y / 1e6))
+    A = np.ones((N, N))
+    dt = 1800.0
+    return Problem(N=N, L=L, const=const, h=H, A=A, wind=problem_two_wind(N, dt, L), ocean=problem_two_ocean(N, L),
+                   v_old=np.zeros((N + 1, N + 1, 2)), dt=dt)
+
+
 CONFIG_NAMES = {
     0: "svN FP64, 64x64 cells (8,450 DOF), one 1800 s step from rest",
     1: "svN FP64, 512x512 cells (526,338 DOF), 10 steps, translating vortex",
