@@ -161,6 +161,37 @@ int svn_set_forcing_host(svn_handle* h, const double* hcell, const double* A,
 int svn_step(svn_handle* h, double dt, double tol, double* out_v, svn_stats* stats);
 int svn_step_host(svn_handle* h, double dt, double tol, double* out_v, svn_stats* stats);
 
+/* ---- Time stepping of the coupled system (Section 3) ----
+ *
+ * svn_transport: the explicit step for concentration and thickness
+ * (Eqs. "model:A", "model:H"; Section 3; A and H cell-wise constant as in
+ * Section 5.1).  Moves the handle's h and A (those of the last
+ * svn_set_forcing or svn_advance) over dt [s] with its v^n by first-order
+ * upwind finite volumes: face normal velocity = mean of the two end nodes,
+ * node velocities on the boundary taken as 0 (v = 0 on the boundary, so no
+ * flux crosses it), explicit Euler split into max(1, ceil(c)) equal
+ * sub-steps where c = dt/dx * max over cells of the summed outflow normal
+ * velocities, and A capped at 1 afterwards.  *substeps (may be NULL)
+ * receives the number of sub-steps.  Errors: SVN_ERR_STATE before
+ * svn_set_forcing, SVN_ERR_ARG for dt <= 0 or more than 10000 sub-steps,
+ * SVN_ERR_NONFINITE for a non-finite velocity; SVN_ERR_ARG also if the
+ * result has h <= 0 (it cannot while every input h > 0).
+ *
+ * svn_get_ice: copies the handle's current h and A (device, N*N each, cell
+ * (i, j) at j*N + i) to caller-owned device buffers.
+ *
+ * svn_advance: one full time step t_n -> t_{n+1}: svn_transport with v^n,
+ * then wind and ocean replaced by the given device node fields at t_{n+1}
+ * (NULL keeps the current field), then the implicit momentum step from v^n
+ * as in svn_step.  On success the solution becomes v^n of the next call
+ * and is also written to out_v (may be NULL).  On a failed momentum step
+ * v^n is left unchanged while h and A stay transported; stats and *substeps
+ * as above. */
+int svn_transport(svn_handle* h, double dt, int* substeps);
+int svn_get_ice(svn_handle* h, double* hcell, double* A);
+int svn_advance(svn_handle* h, double dt, double tol, const double* wind, const double* ocean, double* out_v,
+                svn_stats* stats, int* substeps);
+
 /* Current iterate v and dual state pi (checkpoint / warm restart). */
 int svn_get_state(svn_handle* h, double* v, double* pi);
 int svn_set_state(svn_handle* h, const double* v, const double* pi);

@@ -64,6 +64,10 @@ _SIGS = {
     "svn_set_forcing_host": (c_int, [c_void_p] + [c_void_p] * 5),
     "svn_step": (c_int, [c_void_p, c_double, c_double, c_void_p, ctypes.POINTER(SvnStats)]),
     "svn_step_host": (c_int, [c_void_p, c_double, c_double, c_void_p, ctypes.POINTER(SvnStats)]),
+    "svn_transport": (c_int, [c_void_p, c_double, ctypes.POINTER(c_int)]),
+    "svn_get_ice": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "svn_advance": (c_int, [c_void_p, c_double, c_double, c_void_p, c_void_p, c_void_p, ctypes.POINTER(SvnStats),
+                            ctypes.POINTER(c_int)]),
     "svn_get_state": (c_int, [c_void_p, c_void_p, c_void_p]),
     "svn_set_state": (c_int, [c_void_p, c_void_p, c_void_p]),
     "svn_residual": (c_int, [c_void_p, c_double, c_void_p, c_void_p, P_double]),

@@ -45,6 +45,14 @@ void launch_trial(cudaStream_t s, const Layout& g, const Phys& ph, const double2
                   const double* P, const double* rhoH, const double* fq, const double* voq, const double* pi,
                   double* pi_t, double* eb, double2* R, double* partial_e, double* out_e, double* partial_r);
 
+// ---- transport of A and H (transport.cu) ----
+int transport_courant_blocks(int N);
+// per-block maxima of the outflow Courant number (dt_dx * outflow) into partial
+void launch_transport_courant(cudaStream_t s, int N, double dt_dx, const double* v, double* partial);
+// one explicit upwind sub-step, k = ds/dx; A capped at 1 when cap is set
+void launch_transport_step(cudaStream_t s, int N, double k, bool cap, const double* v, const double* Hin,
+                           const double* Ain, double* Hout, double* Aout);
+
 // ---- stencil / multigrid kernels (mg_kernels.cu) ----
 // y = A x on interior nodes (0 elsewhere); TA accumulates.
 template <typename TS, typename TX, typename TY, typename TA>

@@ -63,6 +63,7 @@ struct svn_handle {
 
   // forcing (caller layout) and precomputed fields
   double *in_h = nullptr, *in_A = nullptr, *in_wind = nullptr, *in_ocean = nullptr, *in_vold = nullptr;
+  double *tr_h = nullptr, *tr_A = nullptr;   // transport ping-pong (N*N each)
   bool have_forcing = false;
   double *P = nullptr, *rhoH = nullptr, *fq = nullptr, *voq = nullptr;
   double cur_dt = -1.0;
@@ -679,6 +680,8 @@ int create_impl(svn_handle* h, const svn_grid* g, const svn_params* p, void* str
   TRY(dalloc(h, &h->in_wind, nv));
   TRY(dalloc(h, &h->in_ocean, nv));
   TRY(dalloc(h, &h->in_vold, nv));
+  TRY(dalloc(h, &h->tr_h, (size_t)g->N * g->N));
+  TRY(dalloc(h, &h->tr_A, (size_t)g->N * g->N));
   TRY(dalloc(h, &h->P, pl));
   TRY(dalloc(h, &h->rhoH, pl));
   TRY(dalloc(h, &h->fq, 8 * pl));
@@ -732,6 +735,7 @@ int create_impl(svn_handle* h, const svn_grid* g, const svn_params* p, void* str
 
 void destroy_impl(svn_handle* h) {
   dfree(h->in_h); dfree(h->in_A); dfree(h->in_wind); dfree(h->in_ocean); dfree(h->in_vold);
+  dfree(h->tr_h); dfree(h->tr_A);
   dfree(h->P); dfree(h->rhoH); dfree(h->fq); dfree(h->voq);
   dfree(h->v); dfree(h->dv); dfree(h->vt); dfree(h->R); dfree(h->rhs); dfree(h->w);
   dfree(h->pi); dfree(h->pi_t); dfree(h->Rt); dfree(h->pi_scratch); dfree(h->eb);
@@ -795,6 +799,48 @@ int set_forcing_impl(svn_handle* h, const double* hc, const double* A, const dou
   TRY(validate_forcing(h));
   h->have_forcing = true;
   h->state_set = false;
+  return SVN_OK;
+}
+
+// Explicit upwind transport of the handle's H and A over dt with its v^n
+// (Eqs. "model:A", "model:H"; Section 3), sub-cycled for the Courant number.
+constexpr int kMaxSubsteps = 10000;
+int transport_impl(svn_handle* h, double dt, int* nsub) {
+  *nsub = 0;
+  if (!h->have_forcing) return fail(h, SVN_ERR_STATE, "svn_set_forcing has not been called");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(h, SVN_ERR_ARG, "dt must be positive and finite");
+  cudaStream_t s = h->stream;
+  const int N = h->grid.N;
+  const double dx = h->g0.dx;
+  if ((size_t)transport_courant_blocks(N) > h->partial_len)
+    return fail(h, SVN_ERR_ARG, "reduction buffer too small for the Courant maximum");
+  launch_transport_courant(s, N, dt / dx, h->in_vold, h->partial);
+  launch_max_final(s, h->partial, transport_courant_blocks(N), h->scal);
+  CKL();
+  double c = 0.0;
+  TRY(sync_read(h, h->scal, 1, &c));
+  if (!std::isfinite(c)) return fail(h, SVN_ERR_NONFINITE, "non-finite velocity in the transport step");
+  const double nd = std::max(1.0, std::ceil(c));
+  if (nd > kMaxSubsteps)
+    return fail(h, SVN_ERR_ARG, "Courant number %g needs more than %d transport sub-steps", c, kMaxSubsteps);
+  const int n = (int)nd;
+  const double k = (dt / n) / dx;
+  double *Hs = h->in_h, *As = h->in_A, *Hd = h->tr_h, *Ad = h->tr_A;
+  for (int q = 0; q < n; ++q) {
+    launch_transport_step(s, N, k, q == n - 1, h->in_vold, Hs, As, Hd, Ad);
+    std::swap(Hs, Hd);
+    std::swap(As, Ad);
+  }
+  if (Hs != h->in_h) {
+    CK(cudaMemcpyAsync(h->in_h, Hs, sizeof(double) * N * (size_t)N, cudaMemcpyDeviceToDevice, s));
+    CK(cudaMemcpyAsync(h->in_A, As, sizeof(double) * N * (size_t)N, cudaMemcpyDeviceToDevice, s));
+  }
+  CKL();
+  h->have_forcing = false;
+  TRY(validate_forcing(h));
+  h->have_forcing = true;
+  h->state_set = false;
+  *nsub = n;
   return SVN_OK;
 }
 
@@ -1040,16 +1086,17 @@ int svn_set_forcing_host(svn_handle* h, const double* hc, const double* A, const
   return set_forcing_impl(h, hc, A, wind, ocean, v_old, true);
 }
 
-static int step_common(svn_handle* h, double dt, double tol, double* out_v, svn_stats* stats, bool host) {
+static int step_common(svn_handle* h, double dt, double tol, double* out_v, svn_stats* stats, bool host,
+                       bool commit = false) {
   if (!h) return SVN_ERR_ARG;
   svn_stats local;
   svn_stats* st = stats ? stats : &local;
   memset(st, 0, sizeof(*st));
   int rc = step_impl(h, dt, tol, st);
   st->status = rc;
+  const Layout& g = h->g0;
+  const size_t nv = 2 * (size_t)(g.N + 1) * (g.N + 1);
   if (out_v && h->v) {
-    const Layout& g = h->g0;
-    const size_t nv = 2 * (size_t)(g.N + 1) * (g.N + 1);
     if (host) {
       double* tmp = (double*)h->rhs;   // scratch of 2 * plane >= nv doubles
       launch_pack_nodes(h->stream, g, h->v, tmp);
@@ -1062,6 +1109,14 @@ static int step_common(svn_handle* h, double dt, double tol, double* out_v, svn_
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess && rc == SVN_OK) rc = fail(h, SVN_ERR_CUDA, "output copy: %s", cudaGetErrorString(e));
   }
+  if (commit && rc == SVN_OK) {
+    // the solution becomes v^n of the next time step
+    launch_pack_nodes(h->stream, g, h->v, h->in_vold);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess) rc = fail(h, SVN_ERR_CUDA, "velocity commit: %s", cudaGetErrorString(e));
+    st->status = rc;
+  }
   return rc;
 }
 
@@ -1071,6 +1126,45 @@ int svn_step(svn_handle* h, double dt, double tol, double* out_v, svn_stats* sta
 
 int svn_step_host(svn_handle* h, double dt, double tol, double* out_v, svn_stats* stats) {
   return step_common(h, dt, tol, out_v, stats, true);
+}
+
+int svn_transport(svn_handle* h, double dt, int* substeps) {
+  if (!h) return SVN_ERR_ARG;
+  int n = 0;
+  const int rc = transport_impl(h, dt, &n);
+  if (substeps) *substeps = n;
+  return rc;
+}
+
+int svn_get_ice(svn_handle* h, double* hcell, double* A) {
+  if (!h || !hcell || !A) return SVN_ERR_ARG;
+  const size_t nc = (size_t)h->grid.N * h->grid.N;
+  CK(cudaMemcpyAsync(hcell, h->in_h, sizeof(double) * nc, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaMemcpyAsync(A, h->in_A, sizeof(double) * nc, cudaMemcpyDeviceToDevice, h->stream));
+  CK(cudaStreamSynchronize(h->stream));
+  return SVN_OK;
+}
+
+int svn_advance(svn_handle* h, double dt, double tol, const double* wind, const double* ocean, double* out_v,
+                svn_stats* stats, int* substeps) {
+  if (!h) return SVN_ERR_ARG;
+  if (stats) memset(stats, 0, sizeof(*stats));
+  int n = 0;
+  int rc = transport_impl(h, dt, &n);
+  if (substeps) *substeps = n;
+  if (rc == SVN_OK && (wind || ocean)) {
+    const size_t nv = 2 * (size_t)(h->grid.N + 1) * (h->grid.N + 1);
+    if (wind) CK(cudaMemcpyAsync(h->in_wind, wind, sizeof(double) * nv, cudaMemcpyDeviceToDevice, h->stream));
+    if (ocean) CK(cudaMemcpyAsync(h->in_ocean, ocean, sizeof(double) * nv, cudaMemcpyDeviceToDevice, h->stream));
+    h->have_forcing = false;
+    rc = validate_forcing(h);
+    if (rc == SVN_OK) h->have_forcing = true;
+  }
+  if (rc != SVN_OK) {
+    if (stats) stats->status = rc;
+    return rc;
+  }
+  return step_common(h, dt, tol, out_v, stats, false, true);
 }
 
 int svn_get_state(svn_handle* h, double* v, double* pi) {

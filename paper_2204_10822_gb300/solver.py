@@ -116,6 +116,38 @@ class Solver:
             self._check(rc)
         return out, st.to_dict()
 
+    # -- time stepping of the coupled system --------------------------------
+    def transport(self, dt: float) -> int:
+        """Explicit upwind transport of the handle's h and A over dt with v^n;
+        returns the number of sub-steps."""
+        n = ctypes.c_int()
+        self._check(self.lib.svn_transport(self.h, dt, ctypes.byref(n)))
+        return n.value
+
+    def ice(self):
+        """Current (h, A) as device tensors of shape (N, N)."""
+        import torch
+        hc = torch.zeros((self.N, self.N), dtype=torch.float64, device="cuda")
+        A = torch.zeros_like(hc)
+        self._check(self.lib.svn_get_ice(self.h, _ptr(hc), _ptr(A)))
+        return hc, A
+
+    def advance(self, dt: float, tol: float, wind=None, ocean=None, out=None, raise_on_error: bool = True):
+        """One time step: transport of h and A with v^n, new wind / ocean
+        (None keeps the current field), implicit momentum step; the solution
+        becomes v^n of the next call.  Returns (v, stats with "substeps")."""
+        out = self._vec() if out is None else out
+        st = capi.SvnStats()
+        n = ctypes.c_int()
+        rc = self.lib.svn_advance(self.h, dt, tol, _ptr(wind) if wind is not None else None,
+                                  _ptr(ocean) if ocean is not None else None, _ptr(out), ctypes.byref(st),
+                                  ctypes.byref(n))
+        if rc != 0 and raise_on_error:
+            self._check(rc)
+        d = st.to_dict()
+        d["substeps"] = n.value
+        return out, d
+
     def get_state(self):
         import torch
         v = self._vec()

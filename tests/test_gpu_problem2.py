@@ -1,0 +1,142 @@
+"""Time stepping of the coupled system on the GPU: the transport of A and H
+(Sections 2, 3, 5.1) and svn_advance, against the oracle.
+
+The transport kernel evaluates the oracle's update in the same order with
+round-to-nearest intrinsics (no FMA contraction), so the comparison is
+bit-exact; the number of sub-steps is an integer decided by the same FP64
+Courant number on both sides.  Several advanced time steps of the paper's
+Problem II (Section 5.3) are compared with the oracle's transport + Newton.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle.newton import newton
+from oracle.transport import transport
+
+pytestmark = pytest.mark.gpu
+
+
+def dev(a):
+    import torch
+    return torch.as_tensor(np.ascontiguousarray(a, dtype=np.float64), device="cuda")
+
+
+def host(t):
+    return t.detach().cpu().numpy()
+
+
+def make_solver(p, **kw):
+    from paper_2204_10822_gb300 import Solver
+    c = p.const
+    return Solver(p.N, p.L, rho_ice=c.rho_ice, rho_a=c.rho_a, rho_o=c.rho_o, Ca=c.Ca, Co=c.Co, f_c=c.f_c,
+                  Pstar=c.Pstar, C=c.C, e=c.e, delta_min=c.delta_min, **kw)
+
+
+def random_state(N, seed, vscale):
+    rng = np.random.default_rng(seed)
+    v = vscale * rng.standard_normal((N + 1, N + 1, 2))      # boundary values too: they must be ignored
+    H = rng.uniform(0.2, 3.0, (N, N))
+    A = rng.uniform(0.3, 1.0, (N, N))
+    A[::3, ::2] = 1.0               # full cells: convergent flow must hit the cap
+    return v, H, A
+
+
+@pytest.mark.parametrize("N,vscale,dt", [(40, 0.2, 1800.0), (40, 3.0, 1800.0), (64, 0.5, 3600.0), (8, 1.0, 900.0)])
+def test_transport_bitwise(N, vscale, dt):
+    L = 512e3
+    v, H, A = random_state(N, N + int(10 * vscale), vscale)
+    p = W.problem_two(N)
+    s = make_solver(p)
+    s.set_forcing(dev(H), dev(A), dev(p.wind), dev(p.ocean), dev(v))
+    n = s.transport(dt)
+    hc, Ac = s.ice()
+    A1, H1, n1 = transport(N, L, dt, v, A, H)
+    assert n == n1
+    if vscale >= 3.0:
+        assert n > 1
+    np.testing.assert_array_equal(host(hc), H1)
+    np.testing.assert_array_equal(host(Ac), A1)
+    assert (A1 == 1.0).any()        # the cap was exercised
+
+
+def test_transport_twice_and_errors():
+    from paper_2204_10822_gb300 import SvnError
+    N = 24
+    v, H, A = random_state(N, 5, 0.3)
+    p = W.problem_two(N)
+    s = make_solver(p)
+    with pytest.raises(SvnError) as e:
+        s.transport(1800.0)
+    assert e.value.status == "SVN_ERR_STATE"
+    s.set_forcing(dev(H), dev(A), dev(p.wind), dev(p.ocean), dev(v))
+    for bad in (0.0, -1.0, float("nan")):
+        with pytest.raises(SvnError) as e:
+            s.transport(bad)
+        assert e.value.status == "SVN_ERR_ARG"
+    s.transport(600.0)
+    s.transport(600.0)
+    hc, Ac = s.ice()
+    A1, H1, _ = transport(N, p.L, 600.0, v, A, H)
+    A2, H2, _ = transport(N, p.L, 600.0, v, A1, H1)
+    np.testing.assert_array_equal(host(hc), H2)
+    np.testing.assert_array_equal(host(Ac), A2)
+    # more than 10000 sub-steps is refused, the fields stay as they were
+    s2 = make_solver(p)
+    s2.set_forcing(dev(H), dev(A), dev(p.wind), dev(p.ocean), dev(1e6 * np.ones_like(v)))
+    with pytest.raises(SvnError) as e:
+        s2.transport(1800.0)
+    assert e.value.status == "SVN_ERR_ARG"
+    hc, Ac = s2.ice()
+    np.testing.assert_array_equal(host(hc), H)
+
+
+def test_advance_matches_oracle_problem_two():
+    # three full time steps of Problem II at 32^2 (FP64 path, tight
+    # tolerances): v, H and A against the oracle's transport + Newton
+    N, steps, tol = 32, 3, 1e-10
+    p = W.problem_two(N)
+    s = make_solver(p, precision=0, krylov_rtol=1e-11, max_krylov=2000)
+    s.set_forcing(dev(p.h), dev(p.A), dev(p.wind), dev(p.ocean), dev(p.v_old))
+    v, H, A = p.v_old.copy(), p.h.copy(), p.A.copy()
+    for n in range(steps):
+        t1 = (n + 1) * p.dt
+        wind = W.problem_two_wind(N, t1)
+        A, H, nsub = transport(N, p.L, p.dt, v, A, H)
+        q = W.Problem(N=N, L=p.L, const=p.const, h=H, A=A, wind=wind, ocean=p.ocean, v_old=v, dt=p.dt)
+        ref = newton(q, tol=tol)
+        assert ref.converged
+        vg, st = s.advance(p.dt, tol, wind=dev(wind))
+        assert st["status"] == "SVN_OK" and st["substeps"] == nsub
+        assert abs(st["newton_iters"] - ref.newton_iters) <= 1, (n, st["newton_iters"], ref.newton_iters)
+        v = ref.v
+        err = np.linalg.norm(host(vg) - v) / np.linalg.norm(v)
+        assert err <= 1e-8, (n, err)
+        hc, Ac = s.ice()
+        np.testing.assert_allclose(host(hc), H, rtol=1e-12, atol=0)
+        np.testing.assert_allclose(host(Ac), A, rtol=1e-12, atol=0)
+    # the ice moved: H is no longer the initial field
+    assert np.abs(H - p.h).max() > 1e-6
+
+
+def test_advance_keeps_velocity_on_failure():
+    # a failed momentum step (max_newton = 1 at a tight tolerance) leaves
+    # v^n = 0 in place, so a following transport moves nothing
+    N = 16
+    p = W.problem_two(N)
+    s = make_solver(p, precision=0, max_newton=1)
+    s.set_forcing(dev(p.h), dev(p.A), dev(p.wind), dev(p.ocean), dev(p.v_old))
+    v1, st = s.advance(p.dt, 1e-12, raise_on_error=False)
+    assert st["status"] == "SVN_ERR_NO_CONVERGENCE"
+    assert float(abs(v1).max()) > 0.0                   # the last iterate is returned
+    assert s.transport(p.dt) == 1
+    hc, Ac = s.ice()
+    np.testing.assert_array_equal(host(hc), p.h)
+    np.testing.assert_array_equal(host(Ac), p.A)
+    # a successful step commits: now the transport moves the ice
+    s2 = make_solver(p, precision=0)
+    s2.set_forcing(dev(p.h), dev(p.A), dev(p.wind), dev(p.ocean), dev(p.v_old))
+    s2.advance(p.dt, 1e-6)
+    s2.transport(p.dt)
+    hc, _ = s2.ice()
+    assert np.abs(host(hc) - p.h).max() > 0.0
