@@ -113,6 +113,8 @@ typedef struct svn_params {
                                in FP32, 0 in BF16 (BF16 rounding of the entries
                                perturbs the near-rigid modes; robust only on
                                coarse grids) */
+  int cheb_degree_coarse;   /* Chebyshev degree on the coarser levels (0, default:
+                               cheb_degree on every level) */
 } svn_params;
 
 typedef struct svn_stats {

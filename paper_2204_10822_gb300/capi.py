@@ -34,7 +34,8 @@ class SvnParams(ctypes.Structure):
         ("ew_eta_max", c_double), ("lmax_iters", c_int), ("lmax_safety", c_double),
         ("learned_rule", c_int), ("method", c_int), ("mg_rebuild", c_int), ("cheb_fuse", c_int),
         ("fused_trial", c_int),
-        ("vcycle_fp32", c_int)]
+        ("vcycle_fp32", c_int),
+        ("cheb_degree_coarse", c_int)]
 
 
 class SvnStats(ctypes.Structure):

@@ -280,6 +280,11 @@ int energy(svn_handle* h, const double2* v, const double2* dv, const double* alp
   return SVN_OK;
 }
 
+// Chebyshev degree used on multigrid level l
+inline int level_degree(const svn_params& p, int l) {
+  return (l > 0 && p.cheb_degree_coarse > 0) ? p.cheb_degree_coarse : p.cheb_degree;
+}
+
 int linearize(svn_handle* h, const double2* v, const double* pi, bool hierarchy = true) {
   const Phys ph = make_phys(h, h->g0, h->cur_dt);
   cudaStream_t s = h->stream;
@@ -326,9 +331,9 @@ int linearize(svn_handle* h, const double2* v, const double* pi, bool hierarchy 
                                                    h->partial, lv.lmax);
     }
     if (h->mixed)
-      launch_cheb_coefs<float>(s, lv.lmax, h->prm.cheb_lo, h->prm.cheb_degree, (float*)lv.cheb);
+      launch_cheb_coefs<float>(s, lv.lmax, h->prm.cheb_lo, level_degree(h->prm, l), (float*)lv.cheb);
     else
-      launch_cheb_coefs<double>(s, lv.lmax, h->prm.cheb_lo, h->prm.cheb_degree, (double*)lv.cheb);
+      launch_cheb_coefs<double>(s, lv.lmax, h->prm.cheb_lo, level_degree(h->prm, l), (double*)lv.cheb);
   }
   CKL();
   Level& lc = h->lv[L - 1];
@@ -402,7 +407,7 @@ void vcycle(svn_handle* h, int l, const TV* b, TV* xout) {
   TV* r = (TV*)lv.r;
   TV* nxt = nullptr;
   using T = typename ScalarOf<TV>::type;
-  const int deg = h->prm.cheb_degree;
+  const int deg = level_degree(h->prm, l);
   const T* coef = (const T*)lv.cheb;
   TV* dalt = (TV*)lv.d2;
   TV* cur = x0;
@@ -647,6 +652,8 @@ int check_params(svn_handle* h, const svn_params* p) {
   if (p->lmax_iters < 0 || p->lmax_iters > 60) return fail(h, SVN_ERR_ARG, "lmax_iters must be in [0, 60]");
   if (p->method != 0 && p->method != 1) return fail(h, SVN_ERR_ARG, "method must be 0 (svN) or 1 (stdN)");
   if (!(p->lmax_safety >= 1.0 && p->lmax_safety < 4.0)) return fail(h, SVN_ERR_ARG, "lmax_safety must be in [1, 4)");
+  if (p->cheb_degree_coarse < 0 || p->cheb_degree_coarse > 16)
+    return fail(h, SVN_ERR_ARG, "cheb_degree_coarse must be in [0, 16]");
   return SVN_OK;
 }
 
@@ -1043,6 +1050,7 @@ int svn_default_params(svn_params* p) {
   p->lmax_iters = 15;
   p->lmax_safety = 1.15;
   p->vcycle_fp32 = 1;
+  p->cheb_degree_coarse = 0;
   p->fused_trial = 1;
   p->learned_rule = 0;
   p->cheb_fuse = 1;

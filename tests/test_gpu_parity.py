@@ -154,6 +154,34 @@ def test_vcycle_parity_fp64():
         assert relmax(z, zo) < 1e-9, (iters, fuse, deg)
 
 
+def test_vcycle_parity_level_degrees():
+    # degree 4 on the finest level, 7 on the coarser ones (cheb_degree_coarse):
+    # the oracle's V-cycle steps with a per-level degree
+    import scipy.linalg as sla
+    N = 64
+    p = W.make_problem(N, seed=7)
+    st = Step(p)
+    s = make_solver(p, coarse_N=8, cheb_degree=4, cheb_degree_coarse=7, cheb_lo=0.1, lmax_iters=15)
+    v = rand_v(N, 7)
+    pi = st.pi_of(v)
+    s.linearize(p.dt, dev(v), dev(pi))
+    levels = mg.build_hierarchy(st.svn_matrix(v, pi), N, coarse_N=8, power_iters=15)
+
+    def cycle(b, l):
+        lv = levels[l]
+        if l == len(levels) - 1:
+            return sla.cho_solve(lv.chol, b)
+        deg = 4 if l == 0 else 7
+        x = mg.chebyshev(lv.A, lv.Dinv, b, np.zeros_like(b), deg, lv.lmax, 0.1)
+        x = x + lv.P @ cycle(lv.P.T @ (b - lv.A @ x), l + 1)
+        return mg.chebyshev(lv.A, lv.Dinv, b, x, deg, lv.lmax, 0.1)
+
+    r = rand_v(N, 9, 1.0)
+    z = host(s.precondition(dev(r)))
+    zo = st.from_free(cycle(st.to_free(r), 0))
+    assert relmax(z, zo) < 1e-9
+
+
 def test_krylov_solve_parity():
     N = 64
     p = W.make_problem(N, seed=6)
