@@ -154,11 +154,10 @@ class ClockSampler:
 SETTINGS = dict(eisenstat_walker=1, krylov_rtol=1e-4, ew_eta_max=0.1, max_krylov=600, cheb_degree=6,
                 cheb_lo=0.02, coarse_N=4, lmax_iters=15)
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2070 MHz
-# DRAM traffic (read + write) per node of the finest-level fused two-step FP32
-# sweep, from the ncu capture in profiles/k_cheb_sweep2_fp32_1024.md (128.46 MB
-# over 1,057,800 nodes); set to None whenever k_cheb_sweep2 changes until it is
-# captured again.
-SWEEP_TRAFFIC_PER_NODE = 128.46e6 / 1_057_800
+# DRAM traffic (read + write) per node of the finest-level two-step FP32 sweep
+# (row-streaming kernel k_cheb_sweep2s), from an ncu capture at 1024^2; None
+# until that kernel is captured (and again whenever it changes).
+SWEEP_TRAFFIC_PER_NODE = None
 
 
 def sweep_bytes_per_node(mixed: bool, fp32_coef: bool) -> int:
@@ -288,13 +287,14 @@ def run_ours(args, rank, world):
             byt = sweep_bytes_per_node(mixed, True) * nodes
             avg_s = ms / 1000.0 / n
             ach = byt / avg_s / 1e9
-            roof = {"kernel": "k_cheb_sweep2 (finest-level fused two-step Chebyshev-Jacobi sweep, %s)" % (
-                        "FP32 stencil, FP32 vectors" if mixed else "FP64"),
+            roof = {"kernel": ("k_cheb_sweep2s (finest-level row-streaming two-step Chebyshev-Jacobi sweep, "
+                               "FP32 stencil, FP32 vectors)" if mixed else
+                               "k_cheb_sweep2 (finest-level fused two-step Chebyshev-Jacobi sweep, FP64)"),
                     "bound": "hbm", "achieved": ach, "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
                     "frac": ach / hbm_peak,
                     "traffic": (SWEEP_TRAFFIC_PER_NODE * (N + 1) * ((N + 1 + 7) // 8 * 8)
                                 if (mixed and SWEEP_TRAFFIC_PER_NODE) else None),
-                    "traffic_source": "ncu capture at 1024^2 scaled by nodes (profiles/k_cheb_sweep2_fp32_1024.md)",
+                    "traffic_source": "ncu capture at 1024^2 scaled by nodes (profiles/k_cheb_sweep2s_fp32_1024.md)",
                     "launches": n, "avg_us": avg_s * 1e6, "algorithmic_bytes_per_launch": byt}
         roof64 = None
         ms, n = prof["apply"]

@@ -105,8 +105,11 @@ typedef struct svn_params {
   int mg_rebuild;           /* rebuild the V-cycle hierarchy (Galerkin levels, smoother
                                data) every mg_rebuild Newton iterations (1 = always);
                                the FP64 outer operator is rebuilt every iteration */
-  int cheb_fuse;            /* 1 (default): two Chebyshev steps per pass (shared-memory
-                               tile with a one-node ring); 0: one step per pass */
+  int cheb_fuse;            /* 1 (default): two Chebyshev steps per pass (row-streaming
+                               warps on levels with N >= 512 in FP32, a shared-memory
+                               tile with a one-node ring elsewhere); 2: two steps per
+                               pass, tile kernel on every level; 3: two steps per pass,
+                               row-streaming on every FP32 level; 0: one step per pass */
   int fused_trial;          /* 1 (default): evaluate Phi, R and pi at the unit step in one
                                fused pass; 0: separate energy / residual / dual passes */
   int vcycle_fp32;          /* mixed precision: 1 (default) stores the V-cycle stencils

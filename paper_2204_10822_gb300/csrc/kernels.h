@@ -80,11 +80,13 @@ template <typename TS, typename TD, typename TV>
 void launch_cheb_sweep(cudaStream_t s, const Layout& g, const TS* st, const TD* dinv,
                        const typename ScalarOf<TV>::type* coef, int step, const TV* xin, TV* xout, TV* d,
                        const TV* b);
-// Steps (step, step + 1) fused; x0 != x2 and d0 != d2.
+// Steps (step, step + 1) fused; x0 != x2 and d0 != d2.  stream: 1 = the
+// row-streaming kernel on FP32 levels with N >= 512, the shared-memory tile
+// kernel elsewhere; 2 = row-streaming on every FP32 level; 0 = tile kernel.
 template <typename TS, typename TD, typename TV>
 void launch_cheb_sweep2(cudaStream_t s, const Layout& g, const TS* st, const TD* dinv,
                         const typename ScalarOf<TV>::type* coef, int step, const TV* x0, TV* x2, const TV* d0,
-                        TV* d2, const TV* b);
+                        TV* d2, const TV* b, int stream);
 template <typename TV>
 void launch_restrict(cudaStream_t s, const Layout& gf, const Layout& gc, const TV* rf, TV* bc);
 template <typename TV>

@@ -6,6 +6,8 @@
 // Templates: TS = stencil storage (double, float, __nv_bfloat16), TD = block-
 // Jacobi storage, TV = vector type (double2 / float2); arithmetic in the
 // vector's scalar type.
+#include <algorithm>
+
 #include "kernels.h"
 
 namespace svn {
@@ -410,6 +412,192 @@ __global__ void __launch_bounds__(256) k_cheb_sweep2(Layout g, const TS* __restr
   x2[n] = mk2<TV>(x1.x + dx, x1.y + dy);
 }
 
+// ---- row-streaming two-step Chebyshev sweep ----------------------------------
+// The same two Chebyshev steps as k_cheb_sweep2, organised for fewer loads: one
+// warp walks up a strip of 32 node columns (kStreamCols output columns and two
+// halo columns on each side) over a chunk of rows.  Per row a lane loads its
+// node's 19 stencil values, block-Jacobi inverse, b and d0 once.  The
+// transposed blocks that couple a node to its W, SW, S and SE neighbours are
+// not loaded again: the W block comes from the neighbouring lane by a warp
+// shuffle, and the S, SW and SE couplings are added to a partial sum for the
+// row above while the row below is processed ("pushed").  Step 1 runs one row
+// ahead of step 2; the next row's data is loaded while the current row is
+// computed.  No shared memory and no barrier.
+constexpr int kStreamCols = 28;
+
+template <typename T>
+__device__ __forceinline__ T shup(T v) { return __shfl_up_sync(0xffffffffu, v, 1); }
+template <typename T>
+__device__ __forceinline__ T shdn(T v) { return __shfl_down_sync(0xffffffffu, v, 1); }
+template <>
+__device__ __forceinline__ float2 shup<float2>(float2 v) { return make_float2(shup(v.x), shup(v.y)); }
+template <>
+__device__ __forceinline__ float2 shdn<float2>(float2 v) { return make_float2(shdn(v.x), shdn(v.y)); }
+template <>
+__device__ __forceinline__ double2 shup<double2>(double2 v) { return make_double2(shup(v.x), shup(v.y)); }
+template <>
+__device__ __forceinline__ double2 shdn<double2>(double2 v) { return make_double2(shdn(v.x), shdn(v.y)); }
+
+template <typename T, typename TV>
+struct StreamRow {
+  T S[NSTEN];
+  T inv[3];
+  TV b, d0;
+};
+
+template <typename TS, typename TD, typename TV>
+__global__ void __launch_bounds__(128) k_cheb_sweep2s(Layout g, const TS* __restrict__ st,
+                                                      const TD* __restrict__ dinv,
+                                                      const typename ScalarOf<TV>::type* __restrict__ coef, int step,
+                                                      const TV* __restrict__ x0, TV* __restrict__ x2,
+                                                      const TV* __restrict__ d0, TV* __restrict__ d2,
+                                                      const TV* __restrict__ b, int rows) {
+  using T = typename ScalarOf<TV>::type;
+  using Row = StreamRow<T, TV>;
+  const int lane = threadIdx.x & 31;
+  const int warp = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int nstrips = (g.n1 + kStreamCols - 1) / kStreamCols;
+  const int strip = warp % nstrips, chunk = warp / nstrips;
+  const int j_lo = chunk * rows;
+  if (j_lo > g.N) return;   // the whole warp
+  const int j_hi = min(j_lo + rows, g.N + 1);
+  const int i = strip * kStreamCols + lane - 2;
+  const bool col_ok = i >= 0 && i <= g.N;
+  const bool out_lane = col_ok && lane >= 2 && lane < 30;
+  const long long pl = g.plane;
+  const T c1a = coef[2 * step], c2a = coef[2 * step + 1];
+  const T c1b = coef[2 * step + 2], c2b = coef[2 * step + 3];
+  const TV zero = mk2<TV>(T(0), T(0));
+
+  auto load_row = [&](int q, Row& r) {
+    const bool ok = col_ok && q >= 0 && q <= g.N;
+    const long long n = ok ? (long long)q * g.ld + i : 0;
+#pragma unroll
+    for (int k = 0; k < NSTEN; ++k) r.S[k] = ok ? ldc<T>(st + k * pl + n) : T(0);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) r.inv[k] = ok ? ldc<T>(dinv + k * pl + n) : T(0);
+    r.b = ok ? b[n] : zero;
+    r.d0 = ok ? d0[n] : zero;
+  };
+  auto load_x0 = [&](int q) {
+    return (col_ok && q >= 0 && q <= g.N) ? x0[(long long)q * g.ld + i] : zero;
+  };
+
+  // carried between rows
+  TV x1p = zero, d1p = zero, x1pW = zero, x1pE = zero, x0W, x0E;
+  T eWp[4] = {T(0), T(0), T(0), T(0)};
+  T a1x = 0, a1y = 0;                          // row q: couplings to row q-1 (x0)
+  T a2px = 0, a2py = 0, a2cx = 0, a2cy = 0;    // rows q-1, q: couplings to the row below (x1)
+
+  // One row: P = row q-1, C = row q (loaded), N = row q+1 (loaded here);
+  // xc, xn = x0 at rows q, q+1; xnn = x0 at row q+2 (loaded here).
+  auto body = [&](int q, Row& P, Row& C, Row& N, TV& xc, TV& xn, TV& xnn) {
+    load_row(q + 1, N);
+    xnn = load_x0(q + 2);
+
+    const TV x0nW = shup(xn), x0nE = shdn(xn);
+    T eW[4], neW[4], nwE[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      eW[k] = shup(C.S[S_E + k]);
+      neW[k] = shup(C.S[S_NE + k]);
+      nwE[k] = shdn(C.S[S_NW + k]);
+    }
+
+    // step 1 at row q
+    TV x1c = zero, d1c = zero;
+    if (q >= j_lo - 1 && is_interior(i, q, g.N)) {
+      const T* S = C.S;
+      T yx = a1x, yy = a1y;
+      yx += S[S_D] * (T)xc.x + S[S_D + 1] * (T)xc.y;
+      yy += S[S_D + 1] * (T)xc.x + S[S_D + 2] * (T)xc.y;
+      yx += S[S_E] * (T)x0E.x + S[S_E + 1] * (T)x0E.y;
+      yy += S[S_E + 2] * (T)x0E.x + S[S_E + 3] * (T)x0E.y;
+      yx += S[S_N] * (T)xn.x + S[S_N + 1] * (T)xn.y;
+      yy += S[S_N + 2] * (T)xn.x + S[S_N + 3] * (T)xn.y;
+      yx += S[S_NE] * (T)x0nE.x + S[S_NE + 1] * (T)x0nE.y;
+      yy += S[S_NE + 2] * (T)x0nE.x + S[S_NE + 3] * (T)x0nE.y;
+      yx += S[S_NW] * (T)x0nW.x + S[S_NW + 1] * (T)x0nW.y;
+      yy += S[S_NW + 2] * (T)x0nW.x + S[S_NW + 3] * (T)x0nW.y;
+      yx += eW[0] * (T)x0W.x + eW[2] * (T)x0W.y;
+      yy += eW[1] * (T)x0W.x + eW[3] * (T)x0W.y;
+      const T rx = (T)C.b.x - yx, ry = (T)C.b.y - yy;
+      const T dx = c1a * (T)C.d0.x + c2a * (C.inv[0] * rx + C.inv[1] * ry);
+      const T dy = c1a * (T)C.d0.y + c2a * (C.inv[1] * rx + C.inv[2] * ry);
+      d1c = mk2<TV>(dx, dy);
+      x1c = mk2<TV>((T)xc.x + dx, (T)xc.y + dy);
+    }
+    // couplings of row q+1 to row q (x0): S, SW, SE blocks, transposed
+    const T n1x = C.S[S_N] * (T)xc.x + C.S[S_N + 2] * (T)xc.y + neW[0] * (T)x0W.x + neW[2] * (T)x0W.y +
+                  nwE[0] * (T)x0E.x + nwE[2] * (T)x0E.y;
+    const T n1y = C.S[S_N + 1] * (T)xc.x + C.S[S_N + 3] * (T)xc.y + neW[1] * (T)x0W.x + neW[3] * (T)x0W.y +
+                  nwE[1] * (T)x0E.x + nwE[3] * (T)x0E.y;
+
+    // step 2 at row q - 1
+    const TV x1W = shup(x1c), x1E = shdn(x1c);
+    const int p = q - 1;
+    if (p >= j_lo && p < j_hi && out_lane) {
+      const long long np = (long long)p * g.ld + i;
+      if (is_interior(i, p, g.N)) {
+        const T* S = P.S;
+        T yx = a2px, yy = a2py;
+        yx += S[S_D] * (T)x1p.x + S[S_D + 1] * (T)x1p.y;
+        yy += S[S_D + 1] * (T)x1p.x + S[S_D + 2] * (T)x1p.y;
+        yx += S[S_E] * (T)x1pE.x + S[S_E + 1] * (T)x1pE.y;
+        yy += S[S_E + 2] * (T)x1pE.x + S[S_E + 3] * (T)x1pE.y;
+        yx += S[S_N] * (T)x1c.x + S[S_N + 1] * (T)x1c.y;
+        yy += S[S_N + 2] * (T)x1c.x + S[S_N + 3] * (T)x1c.y;
+        yx += S[S_NE] * (T)x1E.x + S[S_NE + 1] * (T)x1E.y;
+        yy += S[S_NE + 2] * (T)x1E.x + S[S_NE + 3] * (T)x1E.y;
+        yx += S[S_NW] * (T)x1W.x + S[S_NW + 1] * (T)x1W.y;
+        yy += S[S_NW + 2] * (T)x1W.x + S[S_NW + 3] * (T)x1W.y;
+        yx += eWp[0] * (T)x1pW.x + eWp[2] * (T)x1pW.y;
+        yy += eWp[1] * (T)x1pW.x + eWp[3] * (T)x1pW.y;
+        const T rx = (T)P.b.x - yx, ry = (T)P.b.y - yy;
+        const T dx = c1b * (T)d1p.x + c2b * (P.inv[0] * rx + P.inv[1] * ry);
+        const T dy = c1b * (T)d1p.y + c2b * (P.inv[1] * rx + P.inv[2] * ry);
+        d2[np] = mk2<TV>(dx, dy);
+        x2[np] = mk2<TV>((T)x1p.x + dx, (T)x1p.y + dy);
+      } else {
+        x2[np] = zero;
+      }
+    }
+    // couplings of row q+1 to row q (x1)
+    const T n2x = C.S[S_N] * (T)x1c.x + C.S[S_N + 2] * (T)x1c.y + neW[0] * (T)x1W.x + neW[2] * (T)x1W.y +
+                  nwE[0] * (T)x1E.x + nwE[2] * (T)x1E.y;
+    const T n2y = C.S[S_N + 1] * (T)x1c.x + C.S[S_N + 3] * (T)x1c.y + neW[1] * (T)x1W.x + neW[3] * (T)x1W.y +
+                  nwE[1] * (T)x1E.x + nwE[3] * (T)x1E.y;
+
+    // carry to the next row (the row data rotates by the caller's argument order)
+    a1x = n1x; a1y = n1y;
+    a2px = a2cx; a2py = a2cy;
+    a2cx = n2x; a2cy = n2y;
+    d1p = d1c;
+    x1p = x1c; x1pW = x1W; x1pE = x1E;
+    x0W = x0nW; x0E = x0nE;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) eWp[k] = eW[k];
+  };
+
+  Row ra, rb, rc;
+  TV xa, xb, xc;
+  int q = j_lo - 2;
+  load_row(q, rb);
+  xb = load_x0(q);
+  xc = load_x0(q + 1);
+  x0W = shup(xb);
+  x0E = shdn(xb);
+  // rows rotate through (ra, rb, rc) so that no row data is copied
+  for (;;) {
+    body(q, ra, rb, rc, xb, xc, xa);
+    if (++q > j_hi) break;
+    body(q, rb, rc, ra, xc, xa, xb);
+    if (++q > j_hi) break;
+    body(q, rc, ra, rb, xa, xb, xc);
+    if (++q > j_hi) break;
+  }
+}
+
 __device__ __forceinline__ double pw(int d) { return d == 0 ? 1.0 : 0.5; }
 
 template <typename TV>
@@ -601,6 +789,29 @@ __global__ void k_convert(long long n, const TA* __restrict__ a, TB* __restrict_
 static const dim3 kBlk(32, 8);
 static inline dim3 ngrid(const Layout& g) { return dim3((g.n1 + kBlk.x - 1) / kBlk.x, (g.n1 + kBlk.y - 1) / kBlk.y); }
 
+// Row-streaming sweep: levels with at least kStreamMinN cells per side, FP32
+// vectors.  Rows per warp are chosen so that the launch is one wave of the
+// resident warps (queried once), with at least 16 rows per warp.
+constexpr int kStreamMinN = 512;
+template <typename TS, typename TD, typename TV>
+static int stream_resident_warps() {
+  static const int w = [] {
+    int dev = 0, sms = 0, bps = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_cheb_sweep2s<TS, TD, TV>, 128, 0) != cudaSuccess ||
+        bps < 1)
+      bps = 1;
+    return sms * bps * 4;
+  }();
+  return w;
+}
+static inline int stream_rows(const Layout& g, int resident_warps) {
+  const int nstrips = (g.n1 + kStreamCols - 1) / kStreamCols;
+  const int target_chunks = std::max(1, resident_warps / nstrips);
+  return std::max(16, (g.n1 + target_chunks - 1) / target_chunks);
+}
+
 template <typename TS, typename TX, typename TY, typename TA>
 void launch_apply(cudaStream_t s, const Layout& g, const TS* st, const TX* x, TY* y) {
   note_launch();
@@ -692,8 +903,19 @@ void launch_cheb_sweep(cudaStream_t s, const Layout& g, const TS* st, const TD* 
 template <typename TS, typename TD, typename TV>
 void launch_cheb_sweep2(cudaStream_t s, const Layout& g, const TS* st, const TD* dinv,
                         const typename ScalarOf<TV>::type* coef, int step, const TV* x0, TV* x2, const TV* d0,
-                        TV* d2, const TV* b) {
+                        TV* d2, const TV* b, int stream) {
   note_launch();
+  if constexpr (sizeof(typename ScalarOf<TV>::type) == 4) {
+    if (stream == 2 || (stream == 1 && g.N >= kStreamMinN)) {
+      const int nstrips = (g.n1 + kStreamCols - 1) / kStreamCols;
+      const int rows = stream_rows(g, stream_resident_warps<TS, TD, TV>());
+      const int chunks = (g.n1 + rows - 1) / rows;
+      const long long warps = (long long)nstrips * chunks;
+      const unsigned blocks = (unsigned)((warps * 32 + 127) / 128);
+      k_cheb_sweep2s<TS, TD, TV><<<blocks, 128, 0, s>>>(g, st, dinv, coef, step, x0, x2, d0, d2, b, rows);
+      return;
+    }
+  }
   k_cheb_sweep2<TS, TD, TV><<<ngrid(g), kBlk, 0, s>>>(g, st, dinv, coef, step, x0, x2, d0, d2, b);
 }
 
@@ -757,7 +979,7 @@ void launch_convert_stencil(cudaStream_t s, const Layout& g, const TA* a, TB* b)
   template void launch_coarse_dense<TS>(cudaStream_t, const Layout&, const TS*, double*);                       \
   template void launch_cheb_sweep2<TS, TD, TV>(cudaStream_t, const Layout&, const TS*, const TD*,                \
                                                const typename ScalarOf<TV>::type*, int, const TV*, TV*,          \
-                                               const TV*, TV*, const TV*);
+                                               const TV*, TV*, const TV*, int);
 
 SVN_INST_LEVEL(double, double, double2)
 SVN_INST_LEVEL(__nv_bfloat16, float, float2)

@@ -420,7 +420,8 @@ void vcycle(svn_handle* h, int l, const TV* b, TV* xout) {
       TV* dst = (last && last_dst && last_dst != cur) ? last_dst : (cur == x0 ? x1 : x0);
       SweepTimer tm(h, l, pair ? 2 : 1);
       if (pair) {
-        launch_cheb_sweep2<TS, TD, TV>(s, lv.g, st, dinv, coef, k, cur, dst, d, dalt, b);
+        launch_cheb_sweep2<TS, TD, TV>(s, lv.g, st, dinv, coef, k, cur, dst, d, dalt, b,
+                                       h->prm.cheb_fuse == 1 ? 1 : h->prm.cheb_fuse == 3 ? 2 : 0);
         std::swap(d, dalt);
         k += 2;
       } else {
@@ -652,6 +653,7 @@ int check_params(svn_handle* h, const svn_params* p) {
   if (p->lmax_iters < 0 || p->lmax_iters > 60) return fail(h, SVN_ERR_ARG, "lmax_iters must be in [0, 60]");
   if (p->method != 0 && p->method != 1) return fail(h, SVN_ERR_ARG, "method must be 0 (svN) or 1 (stdN)");
   if (!(p->lmax_safety >= 1.0 && p->lmax_safety < 4.0)) return fail(h, SVN_ERR_ARG, "lmax_safety must be in [1, 4)");
+  if (p->cheb_fuse < 0 || p->cheb_fuse > 3) return fail(h, SVN_ERR_ARG, "cheb_fuse must be 0, 1, 2 or 3");
   if (p->cheb_degree_coarse < 0 || p->cheb_degree_coarse > 16)
     return fail(h, SVN_ERR_ARG, "cheb_degree_coarse must be in [0, 16]");
   return SVN_OK;

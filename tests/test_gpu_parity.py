@@ -182,6 +182,41 @@ def test_vcycle_parity_level_degrees():
     assert relmax(z, zo) < 1e-9
 
 
+@pytest.mark.parametrize("fuse", [2, 3])
+def test_vcycle_parity_mixed_sweeps(fuse):
+    # FP32 V-cycle (mixed precision) against the oracle's FP64 V-cycle, with the
+    # two-step sweeps done by the shared-memory tile kernel (cheb_fuse = 2) or
+    # by the row-streaming kernel on every level (cheb_fuse = 3); FP32
+    # rounding of the stencil and the arithmetic bounds the difference
+    N = 64
+    p = W.make_problem(N, seed=11)
+    st = Step(p)
+    s = make_solver(p, precision="mixed", coarse_N=8, cheb_degree=4, cheb_lo=0.1, lmax_iters=15, cheb_fuse=fuse)
+    v = rand_v(N, 11)
+    pi = st.pi_of(v)
+    s.linearize(p.dt, dev(v), dev(pi))
+    levels = mg.build_hierarchy(st.svn_matrix(v, pi), N, coarse_N=8, power_iters=15)
+    r = rand_v(N, 12, 1.0)
+    z = host(s.precondition(dev(r)))
+    zo = st.from_free(mg.vcycle(levels, st.to_free(r), degree=4, lo=0.1))
+    assert relmax(z, zo) < 1e-4, relmax(z, zo)
+
+
+def test_streaming_sweep_matches_tile_sweep_at_1024():
+    # at 1024^2 the default (row-streaming on the finest levels) and the tile
+    # kernel compute the same V-cycle up to FP32 summation order
+    N = 1024
+    p = W.make_problem(N, seed=13)
+    v = rand_v(N, 13)
+    out = []
+    for fuse in (1, 2):
+        s = make_solver(p, precision="mixed", cheb_degree=6, cheb_lo=0.02, cheb_fuse=fuse)
+        s.linearize(p.dt, dev(v), dev(np.zeros(s.pi_shape)))      # pi = 0 is a valid dual state
+        out.append(host(s.precondition(dev(rand_v(N, 14, 1.0)))))
+        s.close()
+    assert relmax(out[0], out[1]) < 1e-5, relmax(out[0], out[1])
+
+
 def test_krylov_solve_parity():
     N = 64
     p = W.make_problem(N, seed=6)
@@ -213,11 +248,11 @@ def test_step_parity_fp64(N, fused):
     assert stats["status"] == "SVN_OK"
 
 
-@pytest.mark.parametrize("fp32", [1, 0])
-def test_step_parity_mixed(fp32):
+@pytest.mark.parametrize("fp32,fuse", [(1, 1), (0, 1), (1, 3)])
+def test_step_parity_mixed(fp32, fuse):
     p = W.config(0, N=64)
     res = newton(p, tol=1e-10)
-    s = make_solver(p, precision="mixed", vcycle_fp32=fp32)
+    s = make_solver(p, precision="mixed", vcycle_fp32=fp32, cheb_fuse=fuse)
     v, stats = s.step(p.dt, 1e-10)
     err = np.linalg.norm(host(v) - res.v) / np.linalg.norm(res.v)
     assert err <= 1e-6, err
