@@ -106,7 +106,7 @@ typedef struct svn_params {
                                data) every mg_rebuild Newton iterations (1 = always);
                                the FP64 outer operator is rebuilt every iteration */
   int cheb_fuse;            /* 1 (default): two Chebyshev steps per pass (row-streaming
-                               warps on levels with N >= 512 in FP32, a shared-memory
+                               warps on levels with N >= 1024 in FP32, a shared-memory
                                tile with a one-node ring elsewhere); 2: two steps per
                                pass, tile kernel on every level; 3: two steps per pass,
                                row-streaming on every FP32 level; 0: one step per pass */

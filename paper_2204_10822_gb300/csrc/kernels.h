@@ -81,7 +81,7 @@ void launch_cheb_sweep(cudaStream_t s, const Layout& g, const TS* st, const TD* 
                        const typename ScalarOf<TV>::type* coef, int step, const TV* xin, TV* xout, TV* d,
                        const TV* b);
 // Steps (step, step + 1) fused; x0 != x2 and d0 != d2.  stream: 1 = the
-// row-streaming kernel on FP32 levels with N >= 512, the shared-memory tile
+// row-streaming kernel on FP32 levels with N >= 1024, the shared-memory tile
 // kernel elsewhere; 2 = row-streaming on every FP32 level; 0 = tile kernel.
 template <typename TS, typename TD, typename TV>
 void launch_cheb_sweep2(cudaStream_t s, const Layout& g, const TS* st, const TD* dinv,

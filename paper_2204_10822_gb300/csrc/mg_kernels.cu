@@ -792,7 +792,7 @@ static inline dim3 ngrid(const Layout& g) { return dim3((g.n1 + kBlk.x - 1) / kB
 // Row-streaming sweep: levels with at least kStreamMinN cells per side, FP32
 // vectors.  Rows per warp are chosen so that the launch is one wave of the
 // resident warps (queried once), with at least 16 rows per warp.
-constexpr int kStreamMinN = 512;
+constexpr int kStreamMinN = 1024;
 template <typename TS, typename TD, typename TV>
 static int stream_resident_warps() {
   static const int w = [] {
