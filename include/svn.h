@@ -144,7 +144,10 @@ int svn_default_params(svn_params* p);
 
 /* Create a solver for one grid on the current CUDA device.  cuda_stream is a
  * cudaStream_t (NULL = legacy default stream).  Allocates all device
- * workspace (the multigrid hierarchy, FGMRES basis, quadrature state). */
+ * workspace (the multigrid hierarchy, FGMRES basis, quadrature state).  On
+ * failure *out is still set (unless out is NULL or the handle itself could
+ * not be allocated, SVN_ERR_OOM) so that svn_last_error can be read; it owns
+ * no device memory and must be released with svn_destroy. */
 int svn_create(const svn_grid* g, const svn_params* p, void* cuda_stream, svn_handle** out);
 int svn_destroy(svn_handle* h);
 const char* svn_last_error(const svn_handle* h);
@@ -274,7 +277,10 @@ int svn_residual_noalloc(const svn_grid* grid, const svn_params* prm, double dt,
  * advances all of them by one implicit step concurrently from host_threads
  * host threads (<= 0: 8), so that small grids share the GPU.  out_v[i] are
  * device node vectors of instance i's grid; stats (may be NULL) is an array
- * of n.  The first failing instance's code is returned. ---- */
+ * of n.  The first failing instance's code is returned.  On a failed
+ * svn_batch_create *out is still set (unless out is NULL or the batch could
+ * not be allocated): svn_batch_last_error names the failing instance, and
+ * svn_batch_destroy releases the instances created so far. ---- */
 typedef struct svn_batch svn_batch;
 int svn_batch_create(int n, const svn_grid* grids, const svn_params* p, int host_threads, svn_batch** out);
 int svn_batch_destroy(svn_batch* b);
@@ -310,7 +316,11 @@ int svn_get_params(const svn_handle* h, svn_params* p);
  * step on the first nb batch slots; *loss receives the loss (host).
  * svn_attach_net makes svn_step try the network's prediction as v_0 when
  * params.learned (or svn_set_learned) is on; it is used only if its residual
- * is below ||R(v_old)||, else v_old (stats.learned_used / learned_fallback). */
+ * is below ||R(v_old)||, else v_old (stats.learned_used / learned_fallback).
+ * The handle borrows the network (NULL detaches it): destroy the network only
+ * after detaching it or destroying every handle it is attached to.  The
+ * prediction runs on the handle's stream; the network must not be trained
+ * concurrently on another stream. */
 typedef struct svn_net svn_net;
 int svn_net_create(int G, int batch, void* cuda_stream, svn_net** out);
 int svn_net_destroy(svn_net* net);
