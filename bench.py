@@ -156,10 +156,10 @@ SETTINGS = dict(eisenstat_walker=1, krylov_rtol=1e-4, ew_eta_max=0.1, max_krylov
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2070 MHz
 # DRAM traffic (read + write) per node of the finest-level two-step FP32 sweep
 # (row-streaming kernel k_cheb_sweep2s), from the ncu capture at 1024^2 in
-# profiles/k_cheb_sweep2s_fp32_1024.md (140.85 MB read + 8.88 MB written over
+# profiles/k_cheb_sweep2s_fp32_1024.md (140.88 MB read + 8.64 MB written over
 # 1,057,800 padded nodes); set to None whenever that kernel changes until it is
 # captured again.
-SWEEP_TRAFFIC_PER_NODE = (140.851712e6 + 8.878592e6) / 1_057_800
+SWEEP_TRAFFIC_PER_NODE = (140.884992e6 + 8.641024e6) / 1_057_800
 
 
 def sweep_bytes_per_node(mixed: bool, fp32_coef: bool) -> int:

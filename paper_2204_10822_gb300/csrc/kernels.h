@@ -87,6 +87,9 @@ template <typename TS, typename TD, typename TV>
 void launch_cheb_sweep2(cudaStream_t s, const Layout& g, const TS* st, const TD* dinv,
                         const typename ScalarOf<TV>::type* coef, int step, const TV* x0, TV* x2, const TV* d0,
                         TV* d2, const TV* b, int stream);
+// Whether launch_cheb_sweep2 takes the row-streaming kernel on level g for
+// FP32 vectors; only that kernel accepts x0 = d0 = NULL (start from zero).
+bool sweep2_streams(const Layout& g, int stream);
 template <typename TV>
 void launch_restrict(cudaStream_t s, const Layout& gf, const Layout& gc, const TV* rf, TV* bc);
 template <typename TV>

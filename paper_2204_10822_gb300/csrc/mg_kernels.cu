@@ -477,10 +477,10 @@ __global__ void __launch_bounds__(128) k_cheb_sweep2s(Layout g, const TS* __rest
 #pragma unroll
     for (int k = 0; k < 3; ++k) r.inv[k] = ok ? ldc<T>(dinv + k * pl + n) : T(0);
     r.b = ok ? b[n] : zero;
-    r.d0 = ok ? d0[n] : zero;
+    r.d0 = (ok && d0) ? d0[n] : zero;
   };
   auto load_x0 = [&](int q) {
-    return (col_ok && q >= 0 && q <= g.N) ? x0[(long long)q * g.ld + i] : zero;
+    return (x0 && col_ok && q >= 0 && q <= g.N) ? x0[(long long)q * g.ld + i] : zero;
   };
 
   // carried between rows
@@ -806,6 +806,8 @@ static int stream_resident_warps() {
   }();
   return w;
 }
+bool sweep2_streams(const Layout& g, int stream) { return stream == 2 || (stream == 1 && g.N >= kStreamMinN); }
+
 static inline int stream_rows(const Layout& g, int resident_warps) {
   const int nstrips = (g.n1 + kStreamCols - 1) / kStreamCols;
   const int target_chunks = std::max(1, resident_warps / nstrips);
@@ -906,7 +908,7 @@ void launch_cheb_sweep2(cudaStream_t s, const Layout& g, const TS* st, const TD*
                         TV* d2, const TV* b, int stream) {
   note_launch();
   if constexpr (sizeof(typename ScalarOf<TV>::type) == 4) {
-    if (stream == 2 || (stream == 1 && g.N >= kStreamMinN)) {
+    if (sweep2_streams(g, stream)) {
       const int nstrips = (g.n1 + kStreamCols - 1) / kStreamCols;
       const int rows = stream_rows(g, stream_resident_warps<TS, TD, TV>());
       const int chunks = (g.n1 + rows - 1) / rows;

@@ -412,6 +412,7 @@ void vcycle(svn_handle* h, int l, const TV* b, TV* xout) {
   TV* dalt = (TV*)lv.d2;
   TV* cur = x0;
   const bool fuse = h->prm.cheb_fuse != 0;
+  const int smode = h->prm.cheb_fuse == 1 ? 1 : h->prm.cheb_fuse == 3 ? 2 : 0;   // two-step kernel choice
   // Chebyshev steps [k, kend) from cur; the result lands in `last_dst` when given
   auto smooth = [&](int k, int kend, TV* last_dst) {
     while (k < kend) {
@@ -420,8 +421,7 @@ void vcycle(svn_handle* h, int l, const TV* b, TV* xout) {
       TV* dst = (last && last_dst && last_dst != cur) ? last_dst : (cur == x0 ? x1 : x0);
       SweepTimer tm(h, l, pair ? 2 : 1);
       if (pair) {
-        launch_cheb_sweep2<TS, TD, TV>(s, lv.g, st, dinv, coef, k, cur, dst, d, dalt, b,
-                                       h->prm.cheb_fuse == 1 ? 1 : h->prm.cheb_fuse == 3 ? 2 : 0);
+        launch_cheb_sweep2<TS, TD, TV>(s, lv.g, st, dinv, coef, k, cur, dst, d, dalt, b, smode);
         std::swap(d, dalt);
         k += 2;
       } else {
@@ -431,9 +431,16 @@ void vcycle(svn_handle* h, int l, const TV* b, TV* xout) {
       cur = dst;
     }
   };
-  // pre-smoothing from x = 0
-  launch_cheb_zero_start<TS, TD, TV>(s, lv.g, dinv, coef, b, x0, d);
-  smooth(1, deg, nullptr);
+  // pre-smoothing from x = 0: steps 0 and 1 in one streaming pass where that
+  // kernel runs, else step 0 pointwise
+  if (fuse && deg >= 2 && sizeof(T) == 4 && sweep2_streams(lv.g, smode)) {
+    launch_cheb_sweep2<TS, TD, TV>(s, lv.g, st, dinv, coef, 0, nullptr, x0, nullptr, d, b, smode);
+    cur = x0;
+    smooth(2, deg, nullptr);
+  } else {
+    launch_cheb_zero_start<TS, TD, TV>(s, lv.g, dinv, coef, b, x0, d);
+    smooth(1, deg, nullptr);
+  }
   // coarse-grid correction
   launch_residual_stencil<TS, TV>(s, lv.g, st, cur, b, r);
   Level& lc = h->lv[l + 1];
