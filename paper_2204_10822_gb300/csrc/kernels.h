@@ -65,10 +65,11 @@ template <typename TS, typename TD>
 int launch_dinv_gershgorin(cudaStream_t s, const Layout& g, const TS* st, TD* dinv, double* partial, bool bound);
 void launch_max_final(cudaStream_t s, const double* partial, int n, double* out);
 // lambda_max(D^-1 A) ~= safety |x_k| / |x_{k-1}| after k power steps from the
-// checkerboard vector (x0, x1: level vectors used as scratch).
+// checkerboard vector (x0, x1: level vectors used as scratch); stream as for
+// launch_cheb_sweep2 (two steps per row-streaming pass where it applies).
 template <typename TS, typename TD, typename TV>
 void launch_power_lmax(cudaStream_t s, const Layout& g, const TS* st, const TD* dinv, int iters, double safety,
-                       TV* x0, TV* x1, double* partial, double* lmax);
+                       TV* x0, TV* x1, double* partial, double* lmax, int stream);
 // Chebyshev smoothing (Saad Alg. 12.1 on D^-1 A over [lo lmax, lmax]); the
 // step coefficients are computed on the device from lmax (launch_cheb_coefs).
 template <typename T>

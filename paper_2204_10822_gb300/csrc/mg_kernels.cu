@@ -445,7 +445,7 @@ struct StreamRow {
   TV b, d0;
 };
 
-template <typename TS, typename TD, typename TV>
+template <typename TS, typename TD, typename TV, bool kPower>
 __global__ void __launch_bounds__(128) k_cheb_sweep2s(Layout g, const TS* __restrict__ st,
                                                       const TD* __restrict__ dinv,
                                                       const typename ScalarOf<TV>::type* __restrict__ coef, int step,
@@ -465,8 +465,8 @@ __global__ void __launch_bounds__(128) k_cheb_sweep2s(Layout g, const TS* __rest
   const bool col_ok = i >= 0 && i <= g.N;
   const bool out_lane = col_ok && lane >= 2 && lane < 30;
   const long long pl = g.plane;
-  const T c1a = coef[2 * step], c2a = coef[2 * step + 1];
-  const T c1b = coef[2 * step + 2], c2b = coef[2 * step + 3];
+  const T c1a = kPower ? T(0) : coef[2 * step], c2a = kPower ? T(0) : coef[2 * step + 1];
+  const T c1b = kPower ? T(0) : coef[2 * step + 2], c2b = kPower ? T(0) : coef[2 * step + 3];
   const TV zero = mk2<TV>(T(0), T(0));
 
   auto load_row = [&](int q, Row& r) {
@@ -476,8 +476,8 @@ __global__ void __launch_bounds__(128) k_cheb_sweep2s(Layout g, const TS* __rest
     for (int k = 0; k < NSTEN; ++k) r.S[k] = ok ? ldc<T>(st + k * pl + n) : T(0);
 #pragma unroll
     for (int k = 0; k < 3; ++k) r.inv[k] = ok ? ldc<T>(dinv + k * pl + n) : T(0);
-    r.b = ok ? b[n] : zero;
-    r.d0 = (ok && d0) ? d0[n] : zero;
+    r.b = (ok && !kPower) ? b[n] : zero;
+    r.d0 = (ok && !kPower && d0) ? d0[n] : zero;
   };
   auto load_x0 = [&](int q) {
     return (x0 && col_ok && q >= 0 && q <= g.N) ? x0[(long long)q * g.ld + i] : zero;
@@ -521,11 +521,15 @@ __global__ void __launch_bounds__(128) k_cheb_sweep2s(Layout g, const TS* __rest
       yy += S[S_NW + 2] * (T)x0nW.x + S[S_NW + 3] * (T)x0nW.y;
       yx += eW[0] * (T)x0W.x + eW[2] * (T)x0W.y;
       yy += eW[1] * (T)x0W.x + eW[3] * (T)x0W.y;
-      const T rx = (T)C.b.x - yx, ry = (T)C.b.y - yy;
-      const T dx = c1a * (T)C.d0.x + c2a * (C.inv[0] * rx + C.inv[1] * ry);
-      const T dy = c1a * (T)C.d0.y + c2a * (C.inv[1] * rx + C.inv[2] * ry);
-      d1c = mk2<TV>(dx, dy);
-      x1c = mk2<TV>((T)xc.x + dx, (T)xc.y + dy);
+      if constexpr (kPower) {
+        x1c = mk2<TV>(C.inv[0] * yx + C.inv[1] * yy, C.inv[1] * yx + C.inv[2] * yy);
+      } else {
+        const T rx = (T)C.b.x - yx, ry = (T)C.b.y - yy;
+        const T dx = c1a * (T)C.d0.x + c2a * (C.inv[0] * rx + C.inv[1] * ry);
+        const T dy = c1a * (T)C.d0.y + c2a * (C.inv[1] * rx + C.inv[2] * ry);
+        d1c = mk2<TV>(dx, dy);
+        x1c = mk2<TV>((T)xc.x + dx, (T)xc.y + dy);
+      }
     }
     // couplings of row q+1 to row q (x0): S, SW, SE blocks, transposed
     const T n1x = C.S[S_N] * (T)xc.x + C.S[S_N + 2] * (T)xc.y + neW[0] * (T)x0W.x + neW[2] * (T)x0W.y +
@@ -553,11 +557,15 @@ __global__ void __launch_bounds__(128) k_cheb_sweep2s(Layout g, const TS* __rest
         yy += S[S_NW + 2] * (T)x1W.x + S[S_NW + 3] * (T)x1W.y;
         yx += eWp[0] * (T)x1pW.x + eWp[2] * (T)x1pW.y;
         yy += eWp[1] * (T)x1pW.x + eWp[3] * (T)x1pW.y;
-        const T rx = (T)P.b.x - yx, ry = (T)P.b.y - yy;
-        const T dx = c1b * (T)d1p.x + c2b * (P.inv[0] * rx + P.inv[1] * ry);
-        const T dy = c1b * (T)d1p.y + c2b * (P.inv[1] * rx + P.inv[2] * ry);
-        d2[np] = mk2<TV>(dx, dy);
-        x2[np] = mk2<TV>((T)x1p.x + dx, (T)x1p.y + dy);
+        if constexpr (kPower) {
+          x2[np] = mk2<TV>(P.inv[0] * yx + P.inv[1] * yy, P.inv[1] * yx + P.inv[2] * yy);
+        } else {
+          const T rx = (T)P.b.x - yx, ry = (T)P.b.y - yy;
+          const T dx = c1b * (T)d1p.x + c2b * (P.inv[0] * rx + P.inv[1] * ry);
+          const T dy = c1b * (T)d1p.y + c2b * (P.inv[1] * rx + P.inv[2] * ry);
+          d2[np] = mk2<TV>(dx, dy);
+          x2[np] = mk2<TV>((T)x1p.x + dx, (T)x1p.y + dy);
+        }
       } else {
         x2[np] = zero;
       }
@@ -793,13 +801,14 @@ static inline dim3 ngrid(const Layout& g) { return dim3((g.n1 + kBlk.x - 1) / kB
 // vectors.  Rows per warp are chosen so that the launch is one wave of the
 // resident warps (queried once), with at least 16 rows per warp.
 constexpr int kStreamMinN = 1024;
-template <typename TS, typename TD, typename TV>
+template <typename TS, typename TD, typename TV, bool kPower>
 static int stream_resident_warps() {
   static const int w = [] {
     int dev = 0, sms = 0, bps = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) dev = 0;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 152;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_cheb_sweep2s<TS, TD, TV>, 128, 0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, k_cheb_sweep2s<TS, TD, TV, kPower>, 128, 0) !=
+            cudaSuccess ||
         bps < 1)
       bps = 1;
     return sms * bps * 4;
@@ -844,12 +853,31 @@ int launch_dinv_gershgorin(cudaStream_t s, const Layout& g, const TS* st, TD* di
 
 template <typename TS, typename TD, typename TV>
 void launch_power_lmax(cudaStream_t s, const Layout& g, const TS* st, const TD* dinv, int iters, double safety,
-                       TV* x0, TV* x1, double* partial, double* lmax) {
+                       TV* x0, TV* x1, double* partial, double* lmax, int stream) {
   note_launch();
   k_checkerboard<TV><<<ngrid(g), kBlk, 0, s>>>(g, x0);
   TV* a = x0;
   TV* b = x1;
-  for (int k = 0; k < iters; ++k) {
+  int k = 0;
+  if constexpr (sizeof(typename ScalarOf<TV>::type) == 4) {
+    if (sweep2_streams(g, stream)) {
+      // two power steps per row-streaming pass; the last one or two steps
+      // stay single so that x_iters and x_{iters-1} are both at hand
+      const int nstrips = (g.n1 + kStreamCols - 1) / kStreamCols;
+      const int rows = stream_rows(g, stream_resident_warps<TS, TD, TV, true>());
+      const int chunks = (g.n1 + rows - 1) / rows;
+      const unsigned blocks = (unsigned)(((long long)nstrips * chunks * 32 + 127) / 128);
+      for (; iters - k > 2; k += 2) {
+        note_launch();
+        k_cheb_sweep2s<TS, TD, TV, true><<<blocks, 128, 0, s>>>(g, st, dinv, nullptr, 0, a, b, nullptr, nullptr,
+                                                                 nullptr, rows);
+        TV* t = a;
+        a = b;
+        b = t;
+      }
+    }
+  }
+  for (; k < iters; ++k) {
     note_launch();
     k_power_step<TS, TD, TV><<<ngrid(g), kBlk, 0, s>>>(g, st, dinv, a, b);
     TV* t = a;
@@ -867,12 +895,12 @@ void launch_power_lmax(cudaStream_t s, const Layout& g, const TS* st, const TD* 
   k_lmax_from_norms<<<1, 1024, 0, s>>>(partial, partial + nb, (int)nb, safety, lmax);
 }
 template void launch_power_lmax<double, double, double2>(cudaStream_t, const Layout&, const double*, const double*,
-                                                         int, double, double2*, double2*, double*, double*);
+                                                         int, double, double2*, double2*, double*, double*, int);
 template void launch_power_lmax<float, float, float2>(cudaStream_t, const Layout&, const float*, const float*, int,
-                                                       double, float2*, float2*, double*, double*);
+                                                       double, float2*, float2*, double*, double*, int);
 template void launch_power_lmax<__nv_bfloat16, float, float2>(cudaStream_t, const Layout&, const __nv_bfloat16*,
                                                               const float*, int, double, float2*, float2*, double*,
-                                                              double*);
+                                                              double*, int);
 
 void launch_max_final(cudaStream_t s, const double* partial, int n, double* out) {
   note_launch();
@@ -910,11 +938,11 @@ void launch_cheb_sweep2(cudaStream_t s, const Layout& g, const TS* st, const TD*
   if constexpr (sizeof(typename ScalarOf<TV>::type) == 4) {
     if (sweep2_streams(g, stream)) {
       const int nstrips = (g.n1 + kStreamCols - 1) / kStreamCols;
-      const int rows = stream_rows(g, stream_resident_warps<TS, TD, TV>());
+      const int rows = stream_rows(g, stream_resident_warps<TS, TD, TV, false>());
       const int chunks = (g.n1 + rows - 1) / rows;
       const long long warps = (long long)nstrips * chunks;
       const unsigned blocks = (unsigned)((warps * 32 + 127) / 128);
-      k_cheb_sweep2s<TS, TD, TV><<<blocks, 128, 0, s>>>(g, st, dinv, coef, step, x0, x2, d0, d2, b, rows);
+      k_cheb_sweep2s<TS, TD, TV, false><<<blocks, 128, 0, s>>>(g, st, dinv, coef, step, x0, x2, d0, d2, b, rows);
       return;
     }
   }

@@ -301,6 +301,7 @@ int linearize(svn_handle* h, const double2* v, const double* pi, bool hierarchy 
     launch_rap<double, double>(s, h->lv[l - 1].g, h->lv[l].g, h->lv[l - 1].st64, h->lv[l].st64);
   }
   CKL();
+  const int smode = h->prm.cheb_fuse == 1 ? 1 : h->prm.cheb_fuse == 3 ? 2 : 0;   // two-step kernel choice
   for (int l = 0; l < L - 1; ++l) {
     Level& lv = h->lv[l];
     int nb;
@@ -320,15 +321,15 @@ int linearize(svn_handle* h, const double2* v, const double* pi, bool hierarchy 
       if (h->mixed && h->prm.vcycle_fp32)
         launch_power_lmax<float, float, float2>(s, lv.g, lv.st32, (const float*)lv.dinv, h->prm.lmax_iters,
                                                 h->prm.lmax_safety, (float2*)lv.x[0], (float2*)lv.x[1], h->partial,
-                                                lv.lmax);
+                                                lv.lmax, smode);
       else if (h->mixed)
         launch_power_lmax<__nv_bfloat16, float, float2>(s, lv.g, lv.st16, (const float*)lv.dinv, h->prm.lmax_iters,
                                                         h->prm.lmax_safety, (float2*)lv.x[0], (float2*)lv.x[1],
-                                                        h->partial, lv.lmax);
+                                                        h->partial, lv.lmax, smode);
       else
         launch_power_lmax<double, double, double2>(s, lv.g, lv.st64, (const double*)lv.dinv, h->prm.lmax_iters,
                                                    h->prm.lmax_safety, (double2*)lv.x[0], (double2*)lv.x[1],
-                                                   h->partial, lv.lmax);
+                                                   h->partial, lv.lmax, smode);
     }
     if (h->mixed)
       launch_cheb_coefs<float>(s, lv.lmax, h->prm.cheb_lo, level_degree(h->prm, l), (float*)lv.cheb);
