@@ -137,7 +137,7 @@ __global__ void k_pi_init(Layout g, Phys ph, const double2* __restrict__ v, doub
   if (i >= g.N || j >= g.N) return;
   const long long cell = (long long)j * g.ld + i;
   const Corners c = load_corners(v, cell, g.ld);
-  const double idx = 1.0 / ph.dx;
+  const double idx = ph.idx;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     const Qp p = eval_qp(c, qxi(q), qeta(q));
@@ -164,7 +164,7 @@ __global__ void k_residual_cells(Layout g, Phys ph, const double2* __restrict__ 
   const Corners c = load_corners(v, cell, g.ld);
   const double Pdt = ph.dt * P[cell];
   const double rh = rhoH[cell];
-  const double idx = 1.0 / ph.dx;
+  const double idx = ph.idx;
   const double vpw = 0.25 * ph.dx;   // w / dx
   double rx[4] = {0, 0, 0, 0}, ry[4] = {0, 0, 0, 0};
 #pragma unroll
@@ -245,7 +245,7 @@ __global__ void k_energy_cells(Layout g, Phys ph, int k, AlphaSet al, const doub
     const Corners d0 = load_corners(dv, cell, g.ld);
     const double Ph = 0.5 * ph.dt * P[cell];
     const double rh = rhoH[cell];
-    const double idx = 1.0 / ph.dx;
+    const double idx = ph.idx;
     for (int a = 0; a < k; ++a) {
       const double al0 = al.a[a];
       Corners c;
@@ -402,7 +402,7 @@ __global__ void __launch_bounds__(128) k_element_matrices(Layout g, Phys ph, con
   const Corners c = load_corners(v, cell, g.ld);
   const double Pc = P[cell];
   const double rh = rhoH[cell];
-  const double idx = 1.0 / ph.dx;
+  const double idx = ph.idx;
   const double sq2 = 1.4142135623730950488;
   const double ta = ph.ta, tb = ph.tb, s2 = sq2 * ph.tc;
   double A1[4], A2[4], A3[4], A4[4], A5[4], A6[4], Mxx[4], Myy[4], Mxy[4];
@@ -416,9 +416,10 @@ __global__ void __launch_bounds__(128) k_element_matrices(Layout g, Phys ph, con
     const double p0 = pi[(3 * q + 0) * g.plane + cell];
     const double p1 = pi[(3 * q + 1) * g.plane + cell];
     const double p2 = sq2 * pi[(3 * q + 2) * g.plane + cell];
-    const double m = fmax(1.0, sqrt(2.0 * (p0 * p0 + p1 * p1 + p2 * p2)));   // FP64 branch
+    const double pp = 2.0 * (p0 * p0 + p1 * p1 + p2 * p2);
+    const double invm = pp > 1.0 ? rsqrt(pp) : 1.0;   // 1 / max(1, sqrt(2 pi:pi)), the FP64 branch
     const double a = 0.25 * ph.dt * Pc * inv;               // C' = C / 4
-    const double b = 0.25 * ph.dt * Pc * inv * inv / m;
+    const double b = 0.25 * ph.dt * Pc * inv * inv * invm;
     const double C00 = a - 2.0 * b * t0 * p0, C11 = a - 2.0 * b * t1 * p1, C22 = a - 2.0 * b * t2 * p2;
     const double C01 = -b * (t0 * p1 + p0 * t1), C02 = -b * (t0 * p2 + p0 * t2), C12 = -b * (t1 * p2 + p1 * t2);
     A1[q] = ta * ta * C00 + 2.0 * ta * tb * C01 + tb * tb * C11;
@@ -557,7 +558,7 @@ __global__ void k_dual_update(Layout g, Phys ph, double alpha, const double2* __
   const long long cell = (long long)j * g.ld + i;
   const Corners c = load_corners(v, cell, g.ld);
   const Corners d = load_corners(dv, cell, g.ld);
-  const double idx = 1.0 / ph.dx;
+  const double idx = ph.idx;
   const double sq2 = 1.4142135623730950488;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
@@ -572,10 +573,11 @@ __global__ void k_dual_update(Layout g, Phys ph, double alpha, const double2* __
     const double inv = rsqrt(ph.dmin2 + 2.0 * (t0 * t0 + t1 * t1 + t2 * t2));
     double* pq = pi + (long long)(3 * q) * g.plane + cell;
     const double p0 = pq[0], p1 = pq[g.plane], p2 = sq2 * pq[2 * g.plane];
-    const double m = fmax(1.0, sqrt(2.0 * (p0 * p0 + p1 * p1 + p2 * p2)));
+    const double pp = 2.0 * (p0 * p0 + p1 * p1 + p2 * p2);
+    const double invm = pp > 1.0 ? rsqrt(pp) : 1.0;   // 1 / max(1, sqrt(2 pi:pi))
     const double ts = t0 * s0 + t1 * s1 + t2 * s2;
     const double ps = p0 * s0 + p1 * s1 + p2 * s2;
-    const double f = inv * inv / m;
+    const double f = inv * inv * invm;
     const double n0 = -p0 + (t0 + s0) * inv - (ts * p0 + ps * t0) * f;
     const double n1 = -p1 + (t1 + s1) * inv - (ts * p1 + ps * t1) * f;
     const double n2 = -p2 + (t2 + s2) * inv - (ts * p2 + ps * t2) * f;
@@ -605,45 +607,47 @@ __global__ void k_trial_cells(Layout g, Phys ph, const double2* __restrict__ v, 
     const long long cell = (long long)j * g.ld + i;
     const Corners c0 = load_corners(v, cell, g.ld);
     const Corners d0 = load_corners(dv, cell, g.ld);
-    Corners c;
-    c.v00 = make_double2(c0.v00.x + d0.v00.x, c0.v00.y + d0.v00.y);
-    c.v10 = make_double2(c0.v10.x + d0.v10.x, c0.v10.y + d0.v10.y);
-    c.v01 = make_double2(c0.v01.x + d0.v01.x, c0.v01.y + d0.v01.y);
-    c.v11 = make_double2(c0.v11.x + d0.v11.x, c0.v11.y + d0.v11.y);
     const double Pdt = ph.dt * P[cell];
     const double rh = rhoH[cell];
-    const double idx = 1.0 / ph.dx;
+    const double idx = ph.idx;
     const double vpw = 0.25 * ph.dx;
     const double sq2 = 1.4142135623730950488;
     double rx[4] = {0, 0, 0, 0}, ry[4] = {0, 0, 0, 0};
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const double xi = qxi(q), eta = qeta(q);
+      // v and dv at the point; u = v + dv and tau(u) by linearity
+      const Qp pv = eval_qp(c0, xi, eta);
+      const Qp pd = eval_qp(d0, xi, eta);
+      double vxx, vyy, vxy, sxx, syy, sxy;
+      tau_hat(ph, pv, vxx, vyy, vxy);
+      tau_hat(ph, pd, sxx, syy, sxy);
       // dual step at the current point (uses tau(v), Delta(v), tau(dv))
       {
-        const Qp pv = eval_qp(c0, xi, eta);
-        const Qp pd = eval_qp(d0, xi, eta);
-        double txx, tyy, txy, sxx, syy, sxy;
-        tau_hat(ph, pv, txx, tyy, txy);
-        tau_hat(ph, pd, sxx, syy, sxy);
-        const double t0 = txx * idx, t1 = tyy * idx, t2 = sq2 * txy * idx;
+        const double t0 = vxx * idx, t1 = vyy * idx, t2 = sq2 * vxy * idx;
         const double s0 = sxx * idx, s1 = syy * idx, s2 = sq2 * sxy * idx;
         const double inv = rsqrt(ph.dmin2 + 2.0 * (t0 * t0 + t1 * t1 + t2 * t2));
         const double* pq = pi + (long long)(3 * q) * g.plane + cell;
         const double p0 = pq[0], p1 = pq[g.plane], p2 = sq2 * pq[2 * g.plane];
-        const double m = fmax(1.0, sqrt(2.0 * (p0 * p0 + p1 * p1 + p2 * p2)));
+        const double pp = 2.0 * (p0 * p0 + p1 * p1 + p2 * p2);
+        const double invm = pp > 1.0 ? rsqrt(pp) : 1.0;   // 1 / max(1, sqrt(2 pi:pi))
         const double ts = t0 * s0 + t1 * s1 + t2 * s2;
         const double ps = p0 * s0 + p1 * s1 + p2 * s2;
-        const double f = inv * inv / m;
+        const double f = inv * inv * invm;
         double* pt = pi_t + (long long)(3 * q) * g.plane + cell;
         pt[0] = (t0 + s0) * inv - (ts * p0 + ps * t0) * f;
         pt[g.plane] = (t1 + s1) * inv - (ts * p1 + ps * t1) * f;
         pt[2 * g.plane] = ((t2 + s2) * inv - (ts * p2 + ps * t2) * f) * (1.0 / sq2);
       }
       // energy and residual at u = v + dv
-      const Qp p = eval_qp(c, xi, eta);
-      double txx, tyy, txy;
-      tau_hat(ph, p, txx, tyy, txy);
+      Qp p;
+      p.vx = pv.vx + pd.vx;
+      p.vy = pv.vy + pd.vy;
+      p.gxx = pv.gxx + pd.gxx;
+      p.gxy = pv.gxy + pd.gxy;
+      p.gyx = pv.gyx + pd.gyx;
+      p.gyy = pv.gyy + pd.gyy;
+      const double txx = vxx + sxx, tyy = vyy + syy, txy = vxy + sxy;
       const double tt = (txx * txx + tyy * tyy + 2.0 * txy * txy) * idx * idx;
       const double d2 = ph.dmin2 + 2.0 * tt;
       const double inv = rsqrt(d2);

@@ -85,6 +85,7 @@ extern "C" int svn_residual_noalloc(const svn_grid* grid, const svn_params* prm,
   Phys ph;
   ph.dt = dt;
   ph.dx = g.dx;
+  ph.idx = 1.0 / g.dx;
   ph.w = 0.25 * g.dx * g.dx;
   ph.ta = 0.5 * (1.0 + 1.0 / prm->e);
   ph.tb = 0.5 * (1.0 - 1.0 / prm->e);

@@ -214,6 +214,7 @@ Phys make_phys(const svn_handle* h, const Layout& g, double dt) {
   const double e = h->prm.e;
   ph.dt = dt;
   ph.dx = g.dx;
+  ph.idx = 1.0 / g.dx;
   ph.w = 0.25 * g.dx * g.dx;
   ph.ta = 0.5 * (1.0 + 1.0 / e);
   ph.tb = 0.5 * (1.0 - 1.0 / e);

@@ -54,6 +54,7 @@ inline Layout make_layout(int N, double L) {
 struct Phys {
   double dt;
   double dx;
+  double idx;        // 1 / dx
   double w;          // quadrature weight dx^2 / 4
   double ta, tb, tc; // tau-hat coefficients: (1+1/e)/2, (1-1/e)/2, 1/(2e)
   double dmin2;      // Delta_min^2
