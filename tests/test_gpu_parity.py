@@ -202,10 +202,11 @@ def test_vcycle_parity_mixed_sweeps(fuse):
     assert relmax(z, zo) < 1e-4, relmax(z, zo)
 
 
-def test_streaming_sweep_matches_tile_sweep_at_1024():
-    # at 1024^2 the default (row-streaming on the finest levels) and the tile
-    # kernel compute the same V-cycle up to FP32 summation order
-    N = 1024
+@pytest.mark.parametrize("N", [1024, 2048])
+def test_streaming_sweep_matches_tile_sweep(N):
+    # at the sizes where the default takes the row-streaming kernel (finest
+    # levels, and its power mode for lambda_max) it computes the same V-cycle
+    # as the tile kernel up to FP32 summation order
     p = W.make_problem(N, seed=13)
     v = rand_v(N, 13)
     out = []

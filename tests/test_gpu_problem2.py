@@ -42,7 +42,8 @@ def random_state(N, seed, vscale):
     return v, H, A
 
 
-@pytest.mark.parametrize("N,vscale,dt", [(40, 0.2, 1800.0), (40, 3.0, 1800.0), (64, 0.5, 3600.0), (8, 1.0, 900.0)])
+@pytest.mark.parametrize("N,vscale,dt", [(40, 0.2, 1800.0), (40, 3.0, 1800.0), (64, 0.5, 3600.0), (8, 1.0, 900.0),
+                                         (2048, 0.3, 1800.0)])
 def test_transport_bitwise(N, vscale, dt):
     L = 512e3
     v, H, A = random_state(N, N + int(10 * vscale), vscale)
