@@ -116,8 +116,9 @@ def test_advance_matches_oracle_problem_two():
         hc, Ac = s.ice()
         np.testing.assert_allclose(host(hc), H, rtol=1e-12, atol=0)
         np.testing.assert_allclose(host(Ac), A, rtol=1e-12, atol=0)
-    # the ice moved: H is no longer the initial field
+    # the ice moved: H is no longer the initial field, but its volume is kept
     assert np.abs(H - p.h).max() > 1e-6
+    assert abs(float(hc.sum()) - p.h.sum()) <= 1e-13 * p.h.sum()
 
 
 def test_advance_keeps_velocity_on_failure():

@@ -156,3 +156,24 @@ def test_problem_two_fields():
     w = W.problem_two_wind(64, 2 * 86400.0)
     speed = np.sqrt((w ** 2).sum(-1))
     assert 10.9 < speed.max() <= 15 * 100 / 50 / np.e + 1e-9
+
+
+def test_problem_two_steps_conserve_ice_volume():
+    # the coupled oracle time stepping (Section 3: transport with v^n, then
+    # the momentum step) keeps sum H |K| (no flux across the boundary, where
+    # v = 0) while the ice moves; A stays in [0, 1]
+    from oracle.newton import newton
+    N = 16
+    p = W.problem_two(N)
+    v, H, A = p.v_old.copy(), p.h.copy(), p.A.copy()
+    vol0 = H.sum()
+    for n in range(3):
+        A, H, _ = transport(N, p.L, p.dt, v, A, H)
+        q = W.Problem(N=N, L=p.L, const=p.const, h=H, A=A, wind=W.problem_two_wind(N, (n + 1) * p.dt),
+                      ocean=p.ocean, v_old=v, dt=p.dt)
+        r = newton(q, tol=1e-8)
+        assert r.converged
+        v = r.v
+        assert abs(H.sum() - vol0) <= 1e-14 * vol0
+        assert 0.0 <= A.min() and A.max() <= 1.0
+    assert np.abs(H - p.h).max() > 0.0
