@@ -407,7 +407,6 @@ void vcycle(svn_handle* h, int l, const TV* b, TV* xout) {
   TV* x1 = (TV*)lv.x[1];
   TV* d = (TV*)lv.d;
   TV* r = (TV*)lv.r;
-  TV* nxt = nullptr;
   using T = typename ScalarOf<TV>::type;
   const int deg = level_degree(h->prm, l);
   const T* coef = (const T*)lv.cheb;
@@ -451,9 +450,7 @@ void vcycle(svn_handle* h, int l, const TV* b, TV* xout) {
   launch_prolong_add<TV>(s, lv.g, lc.g, (const TV*)lc.x[0], cur);
   // post-smoothing (same polynomial)
   smooth(0, deg, xout);
-  (void)nxt;
   if (cur != xout) cudaMemcpyAsync(xout, cur, sizeof(TV) * lv.g.plane, cudaMemcpyDeviceToDevice, s);
-  (void)nxt;
 }
 
 // Record the V-cycle launches from lv[0].b to lv[0].x[1] on the handle's stream.
