@@ -197,3 +197,14 @@ def test_energy_decreases_each_accepted_step():
     for a, b in zip(phis[:-1], phis[1:]):
         assert b < a or abs(b - a) <= 1e-13 * scale
     assert phis[-1] < phis[0]
+
+
+def test_svn_and_stdn_reach_the_same_minimiser():
+    # Phi is strictly convex (rho H > 0), so both Newton variants must stop at
+    # the same velocity; svN needs fewer iterations (Section 5.2)
+    p = W.config(0, N=24)
+    a = newton(p, tol=1e-10, method="svn")
+    b = newton(p, tol=1e-10, method="stdn", max_newton=200)
+    assert a.converged and b.converged
+    assert np.linalg.norm(a.v - b.v) <= 1e-7 * np.linalg.norm(a.v)
+    assert a.newton_iters < b.newton_iters
