@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison step")
+    ap.add_argument("--no-sweep", action="store_true", help="skip the smaller-Delta_min comparison steps")
+    ap.add_argument("--sweep-delta-min", type=float, nargs="*", default=[5e-10, 1e-10])
     ap.add_argument("--ensemble", action="store_true",
                     help="ensemble workload: 64 instances, N ~ U{128,256,512,1024}, one step each")
     ap.add_argument("--ensemble-size", type=int, default=64)
@@ -171,6 +173,84 @@ def sweep_bytes_per_node(mixed: bool, fp32_coef: bool) -> int:
     return 19 * (4 if fp32_coef else 2) + 3 * 4 + 8 * 5
 
 
+def rel_l2(a, b) -> float:
+    """||a - b|| / ||b|| over all node values (boundary entries are zero in both)."""
+    import torch
+    return float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+
+
+def fp64_comparison(args, p, dev_in, v_mixed, stats_mixed, steps):
+    """The plain FP64 GPU path on the same forcing: timed over `steps` steps with CUDA
+    events (after one warm-up), its solution compared with the mixed one, and one
+    tighter FP64 solve (rel-res 1e-11) as the accuracy reference."""
+    import torch
+    from paper_2204_10822_gb300 import Solver
+
+    N = p.N
+    s64 = Solver(N, p.L, **dict(SETTINGS, precision="fp64"))
+    s64.set_forcing(*dev_in)
+    out64 = torch.zeros_like(v_mixed)
+    s64.step(p.dt, args.tol, out=out64)
+    times, st64 = [], None
+    for _ in range(steps):
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record()
+        _, st64 = s64.step(p.dt, args.tol, out=out64)
+        f1.record()
+        torch.cuda.synchronize()
+        times.append(f0.elapsed_time(f1) / 1000.0)
+    res = {"s_per_step": statistics.mean(times), "s_per_step_min": min(times), "s_per_step_max": max(times),
+           "timed_steps": steps, "newton_iters": st64["newton_iters"], "krylov_iters": st64["krylov_iters_total"],
+           "rel_l2_mixed_vs_fp64": rel_l2(v_mixed, out64)}
+    tight = torch.zeros_like(v_mixed)
+    _, stt = s64.step(p.dt, 1e-11, out=tight, raise_on_error=False)
+    if stt["status"] == "SVN_OK":
+        res["fp64_tight"] = {"tol": 1e-11, "newton_iters": stt["newton_iters"],
+                             "rel_res_final": stt["rel_res_final"]}
+        res["rel_l2_mixed_vs_fp64_tight"] = rel_l2(v_mixed, tight)
+        res["rel_l2_fp64_vs_fp64_tight"] = rel_l2(out64, tight)
+    s64.close()
+    return res
+
+
+def delta_min_sweep(args, p, dev_in):
+    """Mixed vs plain FP64 at the smaller Delta_min of the 2048^2 workload's sweep:
+    one timed step each (after one warm-up), iteration counts and the mixed
+    solution's relative L2 distance from the FP64 one."""
+    import dataclasses
+
+    import torch
+    from paper_2204_10822_gb300 import Solver
+
+    rows = []
+    for dmin in args.sweep_delta_min:
+        row = {"delta_min": dmin}
+        outs = {}
+        for prec in ("mixed", "fp64"):
+            s = Solver(p.N, p.L, **dict(SETTINGS, precision=prec, vcycle_fp32=1 if prec == "mixed" else 0,
+                                        delta_min=dmin))
+            s.set_forcing(*dev_in)
+            o = torch.zeros((p.N + 1, p.N + 1, 2), dtype=torch.float64, device="cuda")
+            _, st = s.step(p.dt, args.tol, out=o, raise_on_error=False)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, st = s.step(p.dt, args.tol, out=o, raise_on_error=False)
+            e1.record()
+            torch.cuda.synchronize()
+            row[prec] = {"s_per_step": e0.elapsed_time(e1) / 1000.0, "status": st["status"],
+                         "newton_iters": st["newton_iters"], "krylov_iters": st["krylov_iters_total"]}
+            outs[prec] = o
+            s.close()
+        row["rel_l2_mixed_vs_fp64"] = rel_l2(outs["mixed"], outs["fp64"])
+        row["speedup"] = row["fp64"]["s_per_step"] / row["mixed"]["s_per_step"]
+        rows.append(row)
+        del outs
+        torch.cuda.empty_cache()
+    return rows
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -256,21 +336,14 @@ def run_ours(args, rank, world):
                "h2d_bytes_per_step": int(sum(x.numel() * 8 for x in host_in)),
                "d2h_bytes_per_step": int(host_out.numel() * 8)}
 
-    # the plain FP64 path on the same workload, for the mixed-vs-FP64 comparison
+    # the plain FP64 path on the same workload, for the mixed-vs-FP64 comparison:
+    # the mixed solution stays in `out`, the FP64 one goes to its own buffer
     fp64 = None
     if mixed and not args.no_fp64:
-        s64 = Solver(N, p.L, **dict(SETTINGS, precision="fp64"))
-        s64.set_forcing(*dev_in)
-        s64.step(p.dt, args.tol, out=out)
-        torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record()
-        _, st64 = s64.step(p.dt, args.tol, out=out)
-        f1.record()
-        torch.cuda.synchronize()
-        fp64 = {"s_per_step": f0.elapsed_time(f1) / 1000.0, "newton_iters": st64["newton_iters"],
-                "krylov_iters": st64["krylov_iters_total"]}
-        s64.close()
+        fp64 = fp64_comparison(args, p, dev_in, out, stats, min(args.steps, 3))
+    sweep = None
+    if mixed and not args.no_fp64 and not args.no_sweep and rank == 0:
+        sweep = delta_min_sweep(args, p, dev_in)
 
     result = None
     if rank == 0:
@@ -305,7 +378,9 @@ def run_ours(args, rank, world):
             ach = 72.0 * nodes / avg_s / 1e12
             roof64 = {"kernel": "k_apply (FP64 outer Jacobian apply, 36 DFMA per node)", "bound": "alu",
                       "achieved": ach, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s", "frac": ach / FP64_PEAK_TFLOPS,
-                      "avg_us": avg_s * 1e6, "launches": n, "hbm_gbs": 184.0 * nodes / avg_s / 1e9}
+                      "avg_us": avg_s * 1e6, "launches": n, "hbm_gbs": 184.0 * nodes / avg_s / 1e9,
+                      "hbm_frac_of_measured": 184.0 * nodes / avg_s / 1e9 / hbm_peak,
+                      "hbm_frac_of_nominal_7900": 184.0 * nodes / avg_s / 1e9 / 7900.0}
         shares = {k: round(prof[k][0] / 1000.0 / elapsed, 4) for k in prof}
         result = {
             "metric": METRIC, **aggregate(tmax, args.steps, world), "unit": UNIT, "n_gpus": world,
@@ -324,6 +399,8 @@ def run_ours(args, rank, world):
                              fallback=[st["learned_fallback"] for st in stats],
                              rule="kept only if ||R(v_pred)|| < ||R(v_old)||") if learned_info else None),
             "speedup_vs_fp64": (fp64["s_per_step"] / (tmax / args.steps)) if fp64 else None,
+            "rel_l2_vs_fp64": fp64["rel_l2_mixed_vs_fp64"] if fp64 else None,
+            "delta_min_sweep": sweep,
         }
     return result
 

@@ -258,9 +258,10 @@ int svn_dual_update(svn_handle* h, double dt, const double* v, const double* dv,
  * It allocates nothing: every intermediate array lives in one file-scope
  * device array of about 16 MB (30 planes of the N = SVN_NOALLOC_MAX_N
  * layout), which every GPU that loads the library holds until the process
- * exits.  The first call on a device looks up that array's address (once per
- * device, with the device current); make that first call before any stream
- * capture.  All calls share the array and it keeps the last call's contents:
+ * exits.  Every call looks up that array's address in the current device's
+ * context (so a call after a device reset still finds it); make a first call
+ * before any stream capture, since the module is loaded on first use.  All
+ * calls share the array and it keeps the last call's contents:
  * calls that overlap on the GPU (several streams or host threads) race.
  * Returns SVN_ERR_ARG for N above the maximum, odd N or bad constants,
  * SVN_ERR_NONFINITE for a non-finite norm, SVN_ERR_CUDA on a CUDA error;
@@ -277,7 +278,8 @@ int svn_residual_noalloc(const svn_grid* grid, const svn_params* prm, double dt,
  * advances all of them by one implicit step concurrently from host_threads
  * host threads (<= 0: 8), so that small grids share the GPU.  out_v[i] are
  * device node vectors of instance i's grid; stats (may be NULL) is an array
- * of n.  The first failing instance's code is returned.  On a failed
+ * of n.  The first failing instance's code is returned, and
+ * svn_batch_last_error names every failing instance (up to 8).  On a failed
  * svn_batch_create *out is still set (unless out is NULL or the batch could
  * not be allocated): svn_batch_last_error names the failing instance, and
  * svn_batch_destroy releases the instances created so far. ---- */
@@ -294,7 +296,8 @@ int svn_batch_step(svn_batch* b, double dt, double tol, double* const* out_v, sv
  * iterations of the current forcing, then times one FGMRES solve of that
  * linearisation for every (degree, lo) pair of Chebyshev smoother settings
  * and keeps the fastest in the handle's parameters (read them back with
- * svn_get_params).  *best_ms (may be NULL) receives the winning time. ---- */
+ * svn_get_params).  *best_ms (may be NULL) receives the winning time.  On an
+ * error the handle keeps the smoother settings it had before the call. ---- */
 int svn_autotune(svn_handle* h, double dt, int probe_newton, const int* degrees, int nd,
                  const double* los, int nl, double* best_ms);
 int svn_get_params(const svn_handle* h, svn_params* p);

@@ -14,7 +14,6 @@
 // so nothing needs clearing.  Calls that overlap on the GPU (on different
 // streams, or from different host threads) race on the array.
 #include <cmath>
-#include <mutex>
 
 #include "../../include/svn.h"
 #include "kernels.h"
@@ -33,22 +32,17 @@ constexpr long long kScratchDoubles = kPlanes * kPlaneMax + kTail;
 
 static __device__ __align__(256) double g_scratch[kScratchDoubles];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-double* g_addr[kMaxDevices] = {};
-
-// Device address of g_scratch on the current device (looked up once per device).
+// Device address of g_scratch in the current device's context, looked up on
+// every call (a cheap table lookup once the module is loaded), so that a call
+// after a device reset or on a re-created primary context never launches with
+// a stale address.
 int scratch_address(double** out) {
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return SVN_ERR_CUDA;
-  if (dev < 0 || dev >= kMaxDevices) return SVN_ERR_ARG;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || p == nullptr) return SVN_ERR_CUDA;
-    g_addr[dev] = static_cast<double*>(p);
+  void* p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || p == nullptr) {
+    cudaGetLastError();
+    return SVN_ERR_CUDA;
   }
-  *out = g_addr[dev];
+  *out = static_cast<double*>(p);
   return SVN_OK;
 }
 

@@ -1383,12 +1383,18 @@ int svn_batch_step(svn_batch* b, double dt, double tol, double* const* out_v, sv
   std::vector<std::thread> pool;
   for (int t = 0; t < b->threads; ++t) pool.emplace_back(worker);
   for (auto& t : pool) t.join();
+  // every failing instance is named in the message; the first one's code is returned
+  int first = SVN_OK, nfail = 0;
+  std::string msg;
   for (int i = 0; i < n; ++i)
     if (rcs[i] != SVN_OK) {
-      b->err = "instance " + std::to_string(i) + ": " + b->hs[i]->err;
-      return rcs[i];
+      if (first == SVN_OK) first = rcs[i];
+      if (++nfail <= 8) msg += (msg.empty() ? "" : "; ") + std::string("instance ") + std::to_string(i) + ": " +
+                               b->hs[i]->err;
     }
-  return SVN_OK;
+  if (nfail > 8) msg += "; ... (" + std::to_string(nfail) + " instances failed)";
+  b->err = msg;
+  return first;
 }
 
 // ---- autotuner --------------------------------------------------------------------
@@ -1415,31 +1421,42 @@ int svn_autotune(svn_handle* h, double dt, int probe_newton, const int* degrees,
   double best = 1e300;
   int bd = saved.cheb_degree;
   double bl = saved.cheb_lo;
-  cudaEvent_t e0, e1;
-  CK(cudaEventCreate(&e0));
-  CK(cudaEventCreate(&e1));
-  for (int a = 0; a < nd; ++a)
-    for (int c = 0; c < nl; ++c) {
-      h->prm.cheb_degree = degrees[a];
-      h->prm.cheb_lo = los[c];
-      h->graph_dirty = true;
-      TRY(linearize(h, h->v, h->pi));
-      int its = 0;
-      TRY(fgmres(h, h->rhs, h->dv, saved.krylov_rtol, saved.max_krylov, &its));   // warm (records the graph)
-      CK(cudaEventRecord(e0, h->stream));
-      TRY(fgmres(h, h->rhs, h->dv, saved.krylov_rtol, saved.max_krylov, &its));
-      CK(cudaEventRecord(e1, h->stream));
-      CK(cudaEventSynchronize(e1));
-      float ms = 0.f;
-      CK(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best) {
-        best = ms;
-        bd = degrees[a];
-        bl = los[c];
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  // every candidate runs inside this lambda, so that an error on any of them
+  // still frees the events and restores the handle's own smoother settings
+  auto sweep = [&]() -> int {
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    for (int a = 0; a < nd; ++a)
+      for (int c = 0; c < nl; ++c) {
+        h->prm.cheb_degree = degrees[a];
+        h->prm.cheb_lo = los[c];
+        h->graph_dirty = true;
+        TRY(linearize(h, h->v, h->pi));
+        int its = 0;
+        TRY(fgmres(h, h->rhs, h->dv, saved.krylov_rtol, saved.max_krylov, &its));   // warm (records the graph)
+        CK(cudaEventRecord(e0, h->stream));
+        TRY(fgmres(h, h->rhs, h->dv, saved.krylov_rtol, saved.max_krylov, &its));
+        CK(cudaEventRecord(e1, h->stream));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+          best = ms;
+          bd = degrees[a];
+          bl = los[c];
+        }
       }
-    }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
+    return SVN_OK;
+  };
+  const int rc = sweep();
+  if (e0) cudaEventDestroy(e0);
+  if (e1) cudaEventDestroy(e1);
+  if (rc != SVN_OK) {
+    h->prm = saved;
+    h->graph_dirty = true;
+    return rc;
+  }
   h->prm.cheb_degree = bd;
   h->prm.cheb_lo = bl;
   h->graph_dirty = true;

@@ -84,9 +84,15 @@ def test_prediction_prolongation_matches_oracle():
     assert np.linalg.norm(v0.cpu().numpy() - exp) <= 3e-2 * np.linalg.norm(exp)
 
 
-def test_training_reduces_loss_and_learned_start_gains():
+def test_training_reduces_loss_and_accepted_guesses_cost_no_iterations():
     """Trains on solver-generated pairs at 64 x 64 and compares Newton
-    iterations with and without the learned start on held-out steps."""
+    iterations with and without the learned start on held-out steps.
+
+    What is asserted: a rejected guess leaves the step exactly as without it
+    (same Newton count), and the guesses the residual rule accepts cost no
+    Newton iterations in total.  The fallback rate and the mean counts are
+    printed; on this problem the residual rule rejects most guesses, so no
+    gain is asserted."""
     from paper_2204_10822_gb300 import Solver
     from paper_2204_10822_gb300.learned import Net, generate_pairs, he_init, train
     G = 64
@@ -112,7 +118,8 @@ def test_training_reduces_loss_and_learned_start_gains():
         s.close()
     print("newton iterations without / with learned start: %.2f / %.2f, fallback rate %.2f" % (
         np.mean(its[False]), np.mean(its[True]), np.mean(fallback)))
-    # the residual rule never lets the guess cost iterations: a rejected guess
-    # leaves the step exactly as without it
     for a, b, fb in zip(its[False], its[True], fallback):
-        assert b <= a or not fb
+        if fb:
+            assert b == a, (a, b)
+    acc = [(a, b) for a, b, fb in zip(its[False], its[True], fallback) if not fb]
+    assert sum(b for _, b in acc) <= sum(a for a, _ in acc), acc

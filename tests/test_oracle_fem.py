@@ -208,3 +208,27 @@ def test_svn_and_stdn_reach_the_same_minimiser():
     assert a.converged and b.converged
     assert np.linalg.norm(a.v - b.v) <= 1e-7 * np.linalg.norm(a.v)
     assert a.newton_iters < b.newton_iters
+
+
+def test_mass_floor_bounds_the_hessian():
+    # Phi_h's Hessian is at least the rho H-weighted Q1 mass matrix, whose
+    # smallest eigenvalue on the free dofs is >= rho H_min (dx/3)^2 (1-D mass
+    # matrix dx/6 tridiag(1, 4, 1) with eigenvalues > dx/3; Kronecker product
+    # in 2-D); the full-size GPU certificate rests on this bound
+    p = W.config(0, N=12)
+    st = Step(p)
+    rng = np.random.default_rng(3)
+    v = np.zeros((13, 13, 2))
+    v[1:-1, 1:-1] = 0.05 * rng.standard_normal((11, 11, 2))
+    for K in (st.stdn_matrix(v), st.svn_matrix(v, st.pi_of(v))):
+        lam = np.linalg.eigvalsh(K.toarray()).min()
+        floor = p.const.rho_ice * p.h.min() * (p.L / p.N) ** 2 / 9.0
+        assert lam >= floor > 0, (lam, floor)
+    # and it is attained up to the weights: with Pstar = Co = 0 the Hessian is
+    # the mass matrix, whose smallest eigenvalue is within 1.5x of the bound
+    c = dataclasses.replace(W.Constants(), Pstar=0.0, Co=0.0)
+    q = W.make_problem(12, seed=1, const=c)
+    q.h[:] = 1.0
+    lam = np.linalg.eigvalsh(Step(q).stdn_matrix(v).toarray()).min()
+    floor = c.rho_ice * (q.L / q.N) ** 2 / 9.0
+    assert floor <= lam <= 1.5 * floor, (lam, floor)
