@@ -30,7 +30,7 @@ if ROOT not in sys.path:
 
 METRIC = "s/implicit step to rel-res 1e-8 @8.4M DOF (mixed precision + learned start)"
 UNIT = "s/step"
-SAMPLE_N = 128        # oracle sample grid for the CPU baseline / reference arm
+SAMPLE_N = 128        # oracle sample grid (same recipe) for the CPU baseline / reference arm
 
 
 def parse():
@@ -73,7 +73,8 @@ def workload_config(args, N):
 
 # ---------------------------------------------------------------------------------------
 def oracle_sample(N: int, steps: int, warmup: int) -> dict:
-    """Time the FP64 oracle on the host cores (single thread), in a subprocess."""
+    """Time full FP64 oracle steps (damped svN, direct solves) on the host cores,
+    in a subprocess: the oracle is a serial program, run on one BLAS thread."""
     code = (
         "import json, os, sys, time; sys.path.insert(0, %r)\n"
         "import workloads as W\n"
@@ -86,17 +87,40 @@ def oracle_sample(N: int, steps: int, warmup: int) -> dict:
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
     out = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, check=True)
-    return json.loads(out.stdout.strip().splitlines()[-1])
+    res = json.loads(out.stdout.strip().splitlines()[-1])
+    res["cpu_model"] = cpu_model()
+    return res
 
 
-def cpu_baseline_obj(N_full: int, steps: int = 1, warmup: int = 0) -> dict:
+def cpu_model() -> str:
+    try:
+        import platform
+        for line in open("/proc/cpuinfo"):
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+        out = subprocess.run(["lscpu"], capture_output=True, text=True).stdout
+        for line in out.splitlines():
+            if line.startswith("Model name"):
+                return line.split(":", 1)[1].strip() + " (" + platform.machine() + ")"
+    except OSError:
+        pass
+    return "unknown"
+
+
+def sample_text(res: dict, N: int) -> str:
+    dof = 2 * (N + 1) ** 2
+    return ("full oracle implicit steps (damped svN to rel-res 1e-8, nested-dissection Cholesky direct solves, "
+            "%d Newton iterations) on the %dx%d-cell instance of the same recipe (%d DOF): %d step(s), mean %.2f s; "
+            "one BLAS thread on %s; measured, not scaled" % (res["newton"], N, N, dof, len(res["times"]),
+                                                               statistics.mean(res["times"]), res["cpu_model"]))
+
+
+def cpu_baseline_obj(steps: int = 1, warmup: int = 0) -> dict:
     res = oracle_sample(SAMPLE_N, steps, warmup)
     t = statistics.mean(res["times"])
-    scale = (N_full + 1) ** 2 / (SAMPLE_N + 1) ** 2
-    return {"value": t * scale, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": "full oracle step (SuperLU direct solves, %d Newton its) at %dx%d cells, %.2f s, scaled "
-                      "x%.1f by DOF to %dx%d (linear: a lower bound for a direct solver)" % (
-                          res["newton"], SAMPLE_N, SAMPLE_N, t, scale, N_full, N_full)}
+    return {"value": t, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample_text(res, SAMPLE_N),
+            "sample_N": SAMPLE_N, "sample_dof": 2 * (SAMPLE_N + 1) ** 2,
+            "sample_dof_per_s": 2 * (SAMPLE_N + 1) ** 2 / t}
 
 
 # ---------------------------------------------------------------------------------------
@@ -182,7 +206,7 @@ def rel_l2(a, b) -> float:
 def fp64_comparison(args, p, dev_in, v_mixed, stats_mixed, steps):
     """The plain FP64 GPU path on the same forcing: timed over `steps` steps with CUDA
     events (after one warm-up), its solution compared with the mixed one, and one
-    tighter FP64 solve (rel-res 1e-11) as the accuracy reference."""
+    tighter FP64 solve (rel-res 1e-10) as the accuracy reference."""
     import torch
     from paper_2204_10822_gb300 import Solver
 
@@ -204,9 +228,9 @@ def fp64_comparison(args, p, dev_in, v_mixed, stats_mixed, steps):
            "timed_steps": steps, "newton_iters": st64["newton_iters"], "krylov_iters": st64["krylov_iters_total"],
            "rel_l2_mixed_vs_fp64": rel_l2(v_mixed, out64)}
     tight = torch.zeros_like(v_mixed)
-    _, stt = s64.step(p.dt, 1e-11, out=tight, raise_on_error=False)
+    _, stt = s64.step(p.dt, 1e-10, out=tight, raise_on_error=False)
     if stt["status"] == "SVN_OK":
-        res["fp64_tight"] = {"tol": 1e-11, "newton_iters": stt["newton_iters"],
+        res["fp64_tight"] = {"tol": 1e-10, "newton_iters": stt["newton_iters"],
                              "rel_res_final": stt["rel_res_final"]}
         res["rel_l2_mixed_vs_fp64_tight"] = rel_l2(v_mixed, tight)
         res["rel_l2_fp64_vs_fp64_tight"] = rel_l2(out64, tight)
@@ -240,7 +264,8 @@ def delta_min_sweep(args, p, dev_in):
             e1.record()
             torch.cuda.synchronize()
             row[prec] = {"s_per_step": e0.elapsed_time(e1) / 1000.0, "status": st["status"],
-                         "newton_iters": st["newton_iters"], "krylov_iters": st["krylov_iters_total"]}
+                         "newton_iters": st["newton_iters"], "krylov_iters": st["krylov_iters_total"],
+                         "direction_retries": st["direction_retries"]}
             outs[prec] = o
             s.close()
         row["rel_l2_mixed_vs_fp64"] = rel_l2(outs["mixed"], outs["fp64"])
@@ -390,6 +415,7 @@ def run_ours(args, rank, world):
             "config": workload_config(args, N),
             "newton_iters": [st["newton_iters"] for st in stats],
             "krylov_iters": [st["krylov_iters_total"] for st in stats],
+            "direction_retries": [st["direction_retries"] for st in stats],
             "rel_res_final": [st["rel_res_final"] for st in stats],
             "krylov_per_newton": stats[0]["krylov_per_newton"],
             "alpha_hist": stats[0]["alpha_hist"],
@@ -523,16 +549,17 @@ def main():
         if rank != 0:
             return 0
         res = oracle_sample(SAMPLE_N, args.steps, args.warmup)
-        t = statistics.mean(res["times"])
-        scale = (args.N + 1) ** 2 / (SAMPLE_N + 1) ** 2
-        val = t * scale
-        cb = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle",
-              "sample": "full oracle step at %dx%d cells per timed step (%.2f s), scaled x%.1f by DOF" % (
-                  SAMPLE_N, SAMPLE_N, t, scale)}
+        val = statistics.mean(res["times"])
+        cb = {"value": val, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample_text(res, SAMPLE_N)}
+        cfg = workload_config(args, SAMPLE_N)
+        cfg["precision"] = "fp64 (CPU oracle)"
+        cfg.pop("l2", None)
+        cfg["note"] = ("the oracle's direct solves make the %dx%d workload hours per step on the host, so each "
+                       "timed step is the same recipe at %dx%d" % (args.N, args.N, SAMPLE_N, SAMPLE_N))
         line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": 1,
                 "steps": args.steps, "warmup": args.warmup, "ms_per_step": val * 1000.0, "higher_is_better": False,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": workload_config(args, args.N), "cpu_baseline": cb,
+                "config": cfg, "cpu_baseline": cb, "times": res["times"], "newton_iters": res["newton"],
                 "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
                 "gpu_launches": 0}
         print(json.dumps(line))
@@ -542,7 +569,7 @@ def main():
         torch.distributed.init_process_group("nccl")
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        cb = cpu_baseline_obj(args.N)
+        cb = cpu_baseline_obj()
     res = run_ours(args, rank, world)
     if rank == 0:
         res["cpu_baseline"] = cb

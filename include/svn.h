@@ -118,6 +118,13 @@ typedef struct svn_params {
                                coarse grids) */
   int cheb_degree_coarse;   /* Chebyshev degree on the coarser levels (0, default:
                                cheb_degree on every level) */
+  double retry_alpha;       /* inexact-Newton safeguard (no counterpart in the paper,
+                               which solves each linearisation directly): when the
+                               line search fails or accepts a step length below
+                               retry_alpha while the Krylov tolerance of the step is
+                               above krylov_rtol, the Newton direction is recomputed
+                               with a 100x tighter tolerance (at most 3 times per
+                               Newton iteration).  Default 1/64; 0 disables it */
 } svn_params;
 
 typedef struct svn_stats {
@@ -134,6 +141,7 @@ typedef struct svn_stats {
   int krylov_per_newton[SVN_MAX_NEWTON];
   double res_hist[SVN_MAX_NEWTON + 1];
   double alpha_hist[SVN_MAX_NEWTON];
+  int direction_retries;    /* Newton directions recomputed by the retry_alpha safeguard */
 } svn_stats;
 
 typedef struct svn_handle svn_handle;

@@ -317,14 +317,18 @@ class Step:
         return m.w * Ke
 
     def assemble(self, Ke):
-        """Global sparse matrix restricted to the free dofs (CSR)."""
+        """Global sparse matrix restricted to the free dofs (CSR): the element
+        entries whose row and column dofs are both free, summed."""
         m = self.mesh
         n = 2 * (m.N + 1) ** 2
-        rows = np.broadcast_to(m.dofs[..., :, None], Ke.shape).ravel()
-        cols = np.broadcast_to(m.dofs[..., None, :], Ke.shape).ravel()
-        K = sp.coo_matrix((Ke.ravel(), (rows, cols)), shape=(n, n)).tocsr()
-        f = m.free_idx
-        return K[f][:, f].tocsr()
+        fmap = np.full(n, -1, dtype=np.int64)
+        fmap[m.free_idx] = np.arange(m.free_idx.size)
+        ld = fmap[m.dofs]                                           # (N, N, 8) free index or -1
+        keep = (ld[..., :, None] >= 0) & (ld[..., None, :] >= 0)
+        rows = np.broadcast_to(ld[..., :, None], Ke.shape)[keep]
+        cols = np.broadcast_to(ld[..., None, :], Ke.shape)[keep]
+        nf = m.free_idx.size
+        return sp.coo_matrix((Ke[keep], (rows, cols)), shape=(nf, nf)).tocsr()
 
     def svn_matrix(self, v, pi):
         """Reduced svN linearisation (Eq. "linearSVNewton" + Eq. "modification")."""

@@ -25,6 +25,7 @@ import math
 import numpy as np
 import scipy.sparse.linalg as spla
 
+from .direct import nd_solve
 from .fem import Step
 
 
@@ -41,11 +42,25 @@ class NewtonResult:
     phi_hist: list = dataclasses.field(default_factory=list)
 
 
-def direct_solve(K, b):
+# above this many dofs the nested-dissection multifrontal Cholesky of
+# ``direct.py`` replaces SuperLU (it is faster from about 128^2 cells on)
+ND_MIN_DOFS = 30000
+
+
+def superlu_solve(K, b):
     """Sparse direct solve (SuperLU with a symmetric fill-reducing ordering)."""
     lu = spla.splu(K.tocsc(), permc_spec="MMD_AT_PLUS_A",
                    options={"SymmetricMode": True})
     return lu.solve(b)
+
+
+def direct_solve(K, b):
+    """Sparse direct solve of a free-dof system: SuperLU on small grids, the
+    nested-dissection multifrontal Cholesky on large ones (both exact up to
+    rounding; pinned against each other)."""
+    if K.shape[0] >= ND_MIN_DOFS:
+        return nd_solve(K, b)
+    return superlu_solve(K, b)
 
 
 def line_search(st: Step, v, dv, res_norm, max_halvings=30, floor=1e-13):

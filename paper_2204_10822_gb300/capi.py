@@ -35,7 +35,8 @@ class SvnParams(ctypes.Structure):
         ("learned_rule", c_int), ("method", c_int), ("mg_rebuild", c_int), ("cheb_fuse", c_int),
         ("fused_trial", c_int),
         ("vcycle_fp32", c_int),
-        ("cheb_degree_coarse", c_int)]
+        ("cheb_degree_coarse", c_int),
+        ("retry_alpha", c_double)]
 
 
 class SvnStats(ctypes.Structure):
@@ -44,7 +45,8 @@ class SvnStats(ctypes.Structure):
                 ("res0", c_double), ("res_final", c_double), ("rel_res_final", c_double), ("seconds", c_double),
                 ("krylov_per_newton", c_int * SVN_MAX_NEWTON),
                 ("res_hist", c_double * (SVN_MAX_NEWTON + 1)),
-                ("alpha_hist", c_double * SVN_MAX_NEWTON)]
+                ("alpha_hist", c_double * SVN_MAX_NEWTON),
+                ("direction_retries", c_int)]
 
     def to_dict(self) -> dict:
         n = self.newton_iters
@@ -53,7 +55,8 @@ class SvnStats(ctypes.Structure):
                 "learned_used": self.learned_used, "learned_fallback": self.learned_fallback,
                 "res0": self.res0, "res_final": self.res_final, "rel_res_final": self.rel_res_final,
                 "seconds": self.seconds, "krylov_per_newton": list(self.krylov_per_newton[:n]),
-                "res_hist": list(self.res_hist[:n + 1]), "alpha_hist": list(self.alpha_hist[:n])}
+                "res_hist": list(self.res_hist[:n + 1]), "alpha_hist": list(self.alpha_hist[:n]),
+                "direction_retries": self.direction_retries}
 
 
 _SIGS = {

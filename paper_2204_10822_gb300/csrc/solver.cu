@@ -662,6 +662,7 @@ int check_params(svn_handle* h, const svn_params* p) {
   if (p->cheb_fuse < 0 || p->cheb_fuse > 3) return fail(h, SVN_ERR_ARG, "cheb_fuse must be 0, 1, 2 or 3");
   if (p->cheb_degree_coarse < 0 || p->cheb_degree_coarse > 16)
     return fail(h, SVN_ERR_ARG, "cheb_degree_coarse must be in [0, 16]");
+  if (!(p->retry_alpha >= 0.0 && p->retry_alpha <= 1.0)) return fail(h, SVN_ERR_ARG, "retry_alpha must be in [0, 1]");
   return SVN_OK;
 }
 
@@ -954,60 +955,79 @@ int step_impl(svn_handle* h, double dt, double tol, svn_stats* st) {
       }
       eta_prev = eta;
     }
-    TRY(fgmres(h, h->rhs, h->dv, eta, p.max_krylov, &kits));
-    st->krylov_per_newton[it] = kits;
-    st->krylov_iters_total += kits;
-    // backtracking on Phi (Section 5.1); the unit step is tried first in one
-    // fused pass that also yields R and pi at the trial point
+    // Inexact Newton safeguard: a loose Krylov tolerance on this ill-conditioned
+    // operator can give a direction along which Phi barely decreases; when the
+    // line search fails or accepts a step shorter than retry_alpha, the
+    // direction is recomputed with a 100x tighter tolerance (down to
+    // krylov_rtol, at most 3 times).
     double alpha = 1.0, phi1 = 0.0, scale1 = 0.0;
-    bool ok = false;
-    int k0 = 0;
-    if (p.fused_trial && p.method == 0) {
-      {
-        Prof pr(h, SVN_K_ENERGY);
-        double* pr_res = h->partial + (size_t)energy_partials(g) * (2 * MAX_ALPHA + 1);
-        launch_trial(s, g, ph, h->v, h->dv, h->P, h->rhoH, h->fq, h->voq, h->pi, h->pi_t, h->eb, h->Rt,
-                     h->partial, h->scal, pr_res);
-        launch_sum_final(s, pr_res, residual_partials(g), h->scal + MAX_ALPHA + 1);
-      }
-      CKL();
-      double out[MAX_ALPHA + 2];
-      TRY(sync_read(h, h->scal, MAX_ALPHA + 2, out));
-      phi1 = out[0];
-      scale1 = out[MAX_ALPHA];
-      const double rt = std::sqrt(out[MAX_ALPHA + 1]);
-      ok = phi1 < phi0 || (std::fabs(phi1 - phi0) <= p.ls_floor * scale0 && rt < r);
-      if (ok) {
-        st->alpha_hist[it] = 1.0;
-        launch_axpy(s, g, 1.0, h->dv, h->v);
+    bool ok = false, committed = false;
+    for (int attempt = 0;; ++attempt) {
+      TRY(fgmres(h, h->rhs, h->dv, eta, p.max_krylov, &kits));
+      st->krylov_per_newton[it] += kits;
+      st->krylov_iters_total += kits;
+      // backtracking on Phi (Section 5.1); the unit step is tried first in one
+      // fused pass that also yields R and pi at the trial point
+      alpha = 1.0;
+      ok = false;
+      int k0 = 0;
+      if (p.fused_trial && p.method == 0) {
+        {
+          Prof pr(h, SVN_K_ENERGY);
+          double* pr_res = h->partial + (size_t)energy_partials(g) * (2 * MAX_ALPHA + 1);
+          launch_trial(s, g, ph, h->v, h->dv, h->P, h->rhoH, h->fq, h->voq, h->pi, h->pi_t, h->eb, h->Rt,
+                       h->partial, h->scal, pr_res);
+          launch_sum_final(s, pr_res, residual_partials(g), h->scal + MAX_ALPHA + 1);
+        }
         CKL();
-        std::swap(h->pi, h->pi_t);
-        std::swap(h->R, h->Rt);
-        r_next = rt;
-        have_r = true;
-        phi0 = phi1;
-        scale0 = scale1;
+        double out[MAX_ALPHA + 2];
+        TRY(sync_read(h, h->scal, MAX_ALPHA + 2, out));
+        phi1 = out[0];
+        scale1 = out[MAX_ALPHA];
+        const double rt = std::sqrt(out[MAX_ALPHA + 1]);
+        ok = phi1 < phi0 || (std::fabs(phi1 - phi0) <= p.ls_floor * scale0 && rt < r);
+        if (ok) {
+          st->alpha_hist[it] = 1.0;
+          launch_axpy(s, g, 1.0, h->dv, h->v);
+          CKL();
+          std::swap(h->pi, h->pi_t);
+          std::swap(h->R, h->Rt);
+          r_next = rt;
+          have_r = true;
+          phi0 = phi1;
+          scale0 = scale1;
+          committed = true;
+          break;
+        }
+        st->halvings_total += 1;
+        alpha = 0.5;
+        k0 = 1;
+      }
+      for (int k = k0; k <= p.max_halvings; ++k) {
+        TRY(energy(h, h->v, h->dv, &alpha, 1, &phi1, &scale1));
+        if (phi1 < phi0) {
+          ok = true;
+        } else if (std::fabs(phi1 - phi0) <= p.ls_floor * scale0) {
+          launch_axpby_to(s, g, h->v, alpha, h->dv, h->vt);
+          CKL();
+          double rn;
+          TRY(residual(h, h->vt, h->w, &rn));
+          ok = rn < r;
+        }
+        if (ok) break;
+        st->halvings_total += 1;
+        alpha *= 0.5;
+      }
+      const bool short_step = !ok || alpha < p.retry_alpha;
+      if (short_step && eta > p.krylov_rtol && attempt < 3) {
+        eta = std::max(p.krylov_rtol, 0.01 * eta);
+        eta_prev = eta;
+        st->direction_retries += 1;
         continue;
       }
-      st->halvings_total += 1;
-      alpha = 0.5;
-      k0 = 1;
+      break;
     }
-    for (int k = k0; k <= p.max_halvings; ++k) {
-      TRY(energy(h, h->v, h->dv, &alpha, 1, &phi1, &scale1));
-      if (phi1 < phi0) {
-        ok = true;
-      } else if (std::fabs(phi1 - phi0) <= p.ls_floor * scale0) {
-        launch_axpby_to(s, g, h->v, alpha, h->dv, h->vt);
-        CKL();
-        double rn;
-        TRY(residual(h, h->vt, h->w, &rn));
-        ok = rn < r;
-      }
-      if (ok) break;
-      st->halvings_total += 1;
-      alpha *= 0.5;
-    }
+    if (committed) continue;
     if (!ok) return fail(h, SVN_ERR_LINESEARCH, "line search failed after %d halvings", p.max_halvings);
     st->alpha_hist[it] = alpha;
     if (p.method == 0) {
@@ -1064,6 +1084,7 @@ int svn_default_params(svn_params* p) {
   p->cheb_fuse = 1;
   p->mg_rebuild = 1;
   p->method = 0;
+  p->retry_alpha = 1.0 / 64.0;
   return SVN_OK;
 }
 

@@ -24,3 +24,5 @@ def test_reference_arm_json_line():
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"]["value"] == d["value"] and d["e2e"]["h2d_bytes_per_step"] == 0
     assert d["config"]["workload"]
+    # the timed sample is named, and nothing is scaled from it
+    assert "128x128" in d["config"]["workload"] and "not scaled" in cb["sample"]

@@ -232,3 +232,37 @@ def test_mass_floor_bounds_the_hessian():
     lam = np.linalg.eigvalsh(Step(q).stdn_matrix(v).toarray()).min()
     floor = c.rho_ice * (q.L / q.N) ** 2 / 9.0
     assert floor <= lam <= 1.5 * floor, (lam, floor)
+
+
+@pytest.mark.parametrize("N", [4, 10, 24, 41 + 1, 66])
+def test_nested_dissection_cholesky_matches_superlu(N):
+    # the multifrontal Cholesky used for large grids solves the same systems as
+    # SuperLU to rounding, on grids whose interior width is odd, even, and
+    # below, at and above the leaf size
+    from oracle.direct import NestedDissection
+    from oracle.newton import superlu_solve
+    p = small_problem(N=N, seed=N)
+    st = Step(p)
+    v = random_velocity(N, 7)
+    rng = np.random.default_rng(N)
+    pi = rng.standard_normal((N, N, 4, 3))            # scaled branch at most points
+    K = st.svn_matrix(v, pi)
+    nd = NestedDissection(N - 1, leaf=4).factor(K)
+    for _ in range(2):
+        b = rng.standard_normal(K.shape[0])
+        x_nd, x_lu = nd.solve(b), superlu_solve(K, b)
+        assert np.linalg.norm(x_nd - x_lu) <= 1e-12 * np.linalg.norm(x_lu)
+        assert np.linalg.norm(K @ x_nd - b) <= 1e-13 * np.linalg.norm(b) * 1e2
+    # every dof is eliminated exactly once
+    own = np.concatenate([f.own for f in nd.fronts])
+    assert np.array_equal(np.sort(own), np.arange(K.shape[0]))
+
+
+def test_newton_count_does_not_depend_on_the_direct_solver():
+    from oracle.direct import nd_solve
+    from oracle.newton import superlu_solve
+    p = W.config(0, N=32)
+    a = newton(p, tol=1e-10, solve=superlu_solve)
+    b = newton(p, tol=1e-10, solve=nd_solve)
+    assert a.newton_iters == b.newton_iters
+    assert np.linalg.norm(a.v - b.v) <= 1e-10 * np.linalg.norm(a.v)
