@@ -180,6 +180,7 @@ __global__ void k_residual_cells(Layout g, Phys ph, const double2* __restrict__ 
     const double Fxx = ph.ta * Sxx + ph.tb * Syy - 0.5 * Pdt;
     const double Fyy = ph.tb * Sxx + ph.ta * Syy - 0.5 * Pdt;
     const double Fxy = 2.0 * ph.tc * Sxy;
+    const double Gxx = vpw * Fxx, Gxy = vpw * Fxy, Gyy = vpw * Fyy;
     // source: rho H v + (-rho H v^n + dt cor - dt tau_atm) - dt Co rho_o |w| w
     const double wx = voq[(2 * q) * g.plane + cell] - p.vx;
     const double wy = voq[(2 * q + 1) * g.plane + cell] - p.vy;
@@ -190,8 +191,12 @@ __global__ void k_residual_cells(Layout g, Phys ph, const double2* __restrict__ 
     for (int k = 0; k < 4; ++k) {
       double n, dxi, deta;
       shape(k, xi, eta, n, dxi, deta);
-      rx[k] += n * sx + vpw * (Fxx * dxi + Fxy * deta);
-      ry[k] += n * sy + vpw * (Fxy * dxi + Fyy * deta);
+      rx[k] = fma(n, sx, rx[k]);
+      rx[k] = fma(dxi, Gxx, rx[k]);
+      rx[k] = fma(deta, Gxy, rx[k]);
+      ry[k] = fma(n, sy, ry[k]);
+      ry[k] = fma(dxi, Gxy, ry[k]);
+      ry[k] = fma(deta, Gyy, ry[k]);
     }
   }
 #pragma unroll
@@ -671,6 +676,7 @@ __global__ void k_trial_cells(Layout g, Phys ph, const double2* __restrict__ v, 
       const double Fxx = ph.ta * Sxx + ph.tb * Syy - 0.5 * Pdt;
       const double Fyy = ph.tb * Sxx + ph.ta * Syy - 0.5 * Pdt;
       const double Fxy = 2.0 * ph.tc * Sxy;
+      const double Gxx = vpw * Fxx, Gxy = vpw * Fxy, Gyy = vpw * Fyy;
       const double dr = ph.dt * ph.cdrag * nw;
       const double sx = ph.w * (rh * p.vx + fx - dr * wx);
       const double sy = ph.w * (rh * p.vy + fy - dr * wy);
@@ -678,8 +684,12 @@ __global__ void k_trial_cells(Layout g, Phys ph, const double2* __restrict__ v, 
       for (int k = 0; k < 4; ++k) {
         double n, dxi, deta;
         shape(k, xi, eta, n, dxi, deta);
-        rx[k] += n * sx + vpw * (Fxx * dxi + Fxy * deta);
-        ry[k] += n * sy + vpw * (Fxy * dxi + Fyy * deta);
+        rx[k] = fma(n, sx, rx[k]);
+        rx[k] = fma(dxi, Gxx, rx[k]);
+        rx[k] = fma(deta, Gxy, rx[k]);
+        ry[k] = fma(n, sy, ry[k]);
+        ry[k] = fma(dxi, Gxy, ry[k]);
+        ry[k] = fma(deta, Gyy, ry[k]);
       }
     }
 #pragma unroll

@@ -71,7 +71,8 @@ __global__ void k_norm2_partial(long long n, const double2* __restrict__ x, doub
   double s = 0.0;
   for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
     const double2 v = x[t];
-    s += v.x * v.x + v.y * v.y;
+    s = fma(v.x, v.x, s);
+    s = fma(v.y, v.y, s);
   }
   s = block_sum(s);
   if (threadIdx.x == 0) partial[blockIdx.x] = s;
@@ -153,7 +154,35 @@ __global__ void k_cast_f2d(long long n, const float2* __restrict__ x, double2* _
   }
 }
 
-// partial[i * nwarps + warp] = sum over the warp's elements of V_i . w
+// Sum of eight per-lane values over the warp by recursive halving: at each of
+// the first three steps a lane keeps half of its values and adds the partner's
+// copy of them (one shuffle per kept value), so the eight totals cost 9
+// shuffle-adds per lane instead of 40.  On return every lane holds the total of
+// value (lane >> 2).
+__device__ __forceinline__ double warp_sum8(const double v[8], int lane) {
+  const bool b0 = lane & 16, b1 = lane & 8, b2 = lane & 4;
+  double u[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const double keep = b0 ? v[k + 4] : v[k];
+    const double give = b0 ? v[k] : v[k + 4];
+    u[k] = keep + __shfl_xor_sync(0xffffffffu, give, 16);
+  }
+  double w[2];
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const double keep = b1 ? u[k + 2] : u[k];
+    const double give = b1 ? u[k] : u[k + 2];
+    w[k] = keep + __shfl_xor_sync(0xffffffffu, give, 8);
+  }
+  double z = (b2 ? w[1] : w[0]) + __shfl_xor_sync(0xffffffffu, b2 ? w[0] : w[1], 4);
+  z += __shfl_xor_sync(0xffffffffu, z, 2);
+  z += __shfl_xor_sync(0xffffffffu, z, 1);
+  return z;
+}
+
+// partial[i * nwarps + warp] = sum over the warp's elements of V_i . w; the
+// basis vectors are taken eight at a time (FMA chains, one warp_sum8 each).
 __global__ void __launch_bounds__(ARN_THREADS) k_multidot(long long n, const double2* __restrict__ V,
                                                           long long vstride, int m, const double2* __restrict__ w,
                                                           double* __restrict__ partial, int nwarps) {
@@ -166,19 +195,27 @@ __global__ void __launch_bounds__(ARN_THREADS) k_multidot(long long n, const dou
     const long long t = base + 32 * e;
     wr[e] = t < n ? w[t] : make_double2(0.0, 0.0);
   }
-  for (int i = 0; i < m; ++i) {
-    const double2* Vi = V + (long long)i * vstride;
-    double s = 0.0;
+  for (int i0 = 0; i0 < m; i0 += 8) {
+    double s[8];
 #pragma unroll
-    for (int e = 0; e < EPT; ++e) {
-      const long long t = base + 32 * e;
-      if (t < n) {
-        const double2 a = Vi[t];
-        s += a.x * wr[e].x + a.y * wr[e].y;
+    for (int c = 0; c < 8; ++c) {
+      s[c] = 0.0;
+      if (i0 + c < m) {
+        const double2* Vi = V + (long long)(i0 + c) * vstride;
+#pragma unroll
+        for (int e = 0; e < EPT; ++e) {
+          const long long t = base + 32 * e;
+          if (t < n) {
+            const double2 a = Vi[t];
+            s[c] = fma(a.x, wr[e].x, s[c]);
+            s[c] = fma(a.y, wr[e].y, s[c]);
+          }
+        }
       }
     }
-    s = warp_sum(s);
-    if (lane == 0 && warp < nwarps) partial[(long long)i * nwarps + warp] = s;
+    const double tot = warp_sum8(s, lane);
+    const int c = lane >> 2;
+    if ((lane & 3) == 0 && i0 + c < m && warp < nwarps) partial[(long long)(i0 + c) * nwarps + warp] = tot;
   }
 }
 
@@ -214,8 +251,8 @@ __global__ void __launch_bounds__(ARN_THREADS) k_update_norm(long long n, const 
       const long long t = base + 32 * e;
       if (t < n) {
         const double2 a = Vi[t];
-        wr[e].x -= hi * a.x;
-        wr[e].y -= hi * a.y;
+        wr[e].x = fma(-hi, a.x, wr[e].x);
+        wr[e].y = fma(-hi, a.y, wr[e].y);
       }
     }
   }
@@ -225,7 +262,8 @@ __global__ void __launch_bounds__(ARN_THREADS) k_update_norm(long long n, const 
     const long long t = base + 32 * e;
     if (t < n) {
       w[t] = wr[e];
-      s += wr[e].x * wr[e].x + wr[e].y * wr[e].y;
+      s = fma(wr[e].x, wr[e].x, s);
+      s = fma(wr[e].y, wr[e].y, s);
     }
   }
   s = warp_sum(s);

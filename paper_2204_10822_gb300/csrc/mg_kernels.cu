@@ -52,15 +52,19 @@ __device__ __forceinline__ void stencil_row(const TS* __restrict__ st, long long
     const TX xq = x[q];
     const TA b0 = ldc<TA>(st + (slot + 0) * pl + n), b1 = ldc<TA>(st + (slot + 1) * pl + n);
     const TA b2 = ldc<TA>(st + (slot + 2) * pl + n), b3 = ldc<TA>(st + (slot + 3) * pl + n);
-    yx += b0 * (TA)xq.x + b1 * (TA)xq.y;
-    yy += b2 * (TA)xq.x + b3 * (TA)xq.y;
+    yx = fma(b0, (TA)xq.x, yx);
+    yx = fma(b1, (TA)xq.y, yx);
+    yy = fma(b2, (TA)xq.x, yy);
+    yy = fma(b3, (TA)xq.y, yy);
   };
   auto bwd = [&](int slot, long long q) {   // block stored at q, used transposed
     const TX xq = x[q];
     const TA b0 = ldc<TA>(st + (slot + 0) * pl + q), b1 = ldc<TA>(st + (slot + 1) * pl + q);
     const TA b2 = ldc<TA>(st + (slot + 2) * pl + q), b3 = ldc<TA>(st + (slot + 3) * pl + q);
-    yx += b0 * (TA)xq.x + b2 * (TA)xq.y;
-    yy += b1 * (TA)xq.x + b3 * (TA)xq.y;
+    yx = fma(b0, (TA)xq.x, yx);
+    yx = fma(b2, (TA)xq.y, yx);
+    yy = fma(b1, (TA)xq.x, yy);
+    yy = fma(b3, (TA)xq.y, yy);
   };
   fwd(S_E, n + 1);
   fwd(S_N, n + ld);
@@ -86,16 +90,20 @@ __device__ __forceinline__ void stencil_row_f(const TS* __restrict__ st, long lo
     const auto xq = xf(di, dj);
     const TA b0 = ldc<TA>(st + (slot + 0) * pl + n), b1 = ldc<TA>(st + (slot + 1) * pl + n);
     const TA b2 = ldc<TA>(st + (slot + 2) * pl + n), b3 = ldc<TA>(st + (slot + 3) * pl + n);
-    yx += b0 * (TA)xq.x + b1 * (TA)xq.y;
-    yy += b2 * (TA)xq.x + b3 * (TA)xq.y;
+    yx = fma(b0, (TA)xq.x, yx);
+    yx = fma(b1, (TA)xq.y, yx);
+    yy = fma(b2, (TA)xq.x, yy);
+    yy = fma(b3, (TA)xq.y, yy);
   };
   auto bwd = [&](int slot, int di, int dj) {
     const auto xq = xf(di, dj);
     const long long q = n + (long long)dj * ld + di;
     const TA b0 = ldc<TA>(st + (slot + 0) * pl + q), b1 = ldc<TA>(st + (slot + 1) * pl + q);
     const TA b2 = ldc<TA>(st + (slot + 2) * pl + q), b3 = ldc<TA>(st + (slot + 3) * pl + q);
-    yx += b0 * (TA)xq.x + b2 * (TA)xq.y;
-    yy += b1 * (TA)xq.x + b3 * (TA)xq.y;
+    yx = fma(b0, (TA)xq.x, yx);
+    yx = fma(b2, (TA)xq.y, yx);
+    yy = fma(b1, (TA)xq.x, yy);
+    yy = fma(b3, (TA)xq.y, yy);
   };
   fwd(S_E, 1, 0);
   fwd(S_N, 0, 1);
@@ -509,18 +517,30 @@ __global__ void __launch_bounds__(128) k_cheb_sweep2s(Layout g, const TS* __rest
     if (q >= j_lo - 1 && is_interior(i, q, g.N)) {
       const T* S = C.S;
       T yx = a1x, yy = a1y;
-      yx += S[S_D] * (T)xc.x + S[S_D + 1] * (T)xc.y;
-      yy += S[S_D + 1] * (T)xc.x + S[S_D + 2] * (T)xc.y;
-      yx += S[S_E] * (T)x0E.x + S[S_E + 1] * (T)x0E.y;
-      yy += S[S_E + 2] * (T)x0E.x + S[S_E + 3] * (T)x0E.y;
-      yx += S[S_N] * (T)xn.x + S[S_N + 1] * (T)xn.y;
-      yy += S[S_N + 2] * (T)xn.x + S[S_N + 3] * (T)xn.y;
-      yx += S[S_NE] * (T)x0nE.x + S[S_NE + 1] * (T)x0nE.y;
-      yy += S[S_NE + 2] * (T)x0nE.x + S[S_NE + 3] * (T)x0nE.y;
-      yx += S[S_NW] * (T)x0nW.x + S[S_NW + 1] * (T)x0nW.y;
-      yy += S[S_NW + 2] * (T)x0nW.x + S[S_NW + 3] * (T)x0nW.y;
-      yx += eW[0] * (T)x0W.x + eW[2] * (T)x0W.y;
-      yy += eW[1] * (T)x0W.x + eW[3] * (T)x0W.y;
+      yx = fma(S[S_D], (T)xc.x, yx);
+      yx = fma(S[S_D + 1], (T)xc.y, yx);
+      yy = fma(S[S_D + 1], (T)xc.x, yy);
+      yy = fma(S[S_D + 2], (T)xc.y, yy);
+      yx = fma(S[S_E], (T)x0E.x, yx);
+      yx = fma(S[S_E + 1], (T)x0E.y, yx);
+      yy = fma(S[S_E + 2], (T)x0E.x, yy);
+      yy = fma(S[S_E + 3], (T)x0E.y, yy);
+      yx = fma(S[S_N], (T)xn.x, yx);
+      yx = fma(S[S_N + 1], (T)xn.y, yx);
+      yy = fma(S[S_N + 2], (T)xn.x, yy);
+      yy = fma(S[S_N + 3], (T)xn.y, yy);
+      yx = fma(S[S_NE], (T)x0nE.x, yx);
+      yx = fma(S[S_NE + 1], (T)x0nE.y, yx);
+      yy = fma(S[S_NE + 2], (T)x0nE.x, yy);
+      yy = fma(S[S_NE + 3], (T)x0nE.y, yy);
+      yx = fma(S[S_NW], (T)x0nW.x, yx);
+      yx = fma(S[S_NW + 1], (T)x0nW.y, yx);
+      yy = fma(S[S_NW + 2], (T)x0nW.x, yy);
+      yy = fma(S[S_NW + 3], (T)x0nW.y, yy);
+      yx = fma(eW[0], (T)x0W.x, yx);
+      yx = fma(eW[2], (T)x0W.y, yx);
+      yy = fma(eW[1], (T)x0W.x, yy);
+      yy = fma(eW[3], (T)x0W.y, yy);
       if constexpr (kPower) {
         x1c = mk2<TV>(C.inv[0] * yx + C.inv[1] * yy, C.inv[1] * yx + C.inv[2] * yy);
       } else {
@@ -545,18 +565,30 @@ __global__ void __launch_bounds__(128) k_cheb_sweep2s(Layout g, const TS* __rest
       if (is_interior(i, p, g.N)) {
         const T* S = P.S;
         T yx = a2px, yy = a2py;
-        yx += S[S_D] * (T)x1p.x + S[S_D + 1] * (T)x1p.y;
-        yy += S[S_D + 1] * (T)x1p.x + S[S_D + 2] * (T)x1p.y;
-        yx += S[S_E] * (T)x1pE.x + S[S_E + 1] * (T)x1pE.y;
-        yy += S[S_E + 2] * (T)x1pE.x + S[S_E + 3] * (T)x1pE.y;
-        yx += S[S_N] * (T)x1c.x + S[S_N + 1] * (T)x1c.y;
-        yy += S[S_N + 2] * (T)x1c.x + S[S_N + 3] * (T)x1c.y;
-        yx += S[S_NE] * (T)x1E.x + S[S_NE + 1] * (T)x1E.y;
-        yy += S[S_NE + 2] * (T)x1E.x + S[S_NE + 3] * (T)x1E.y;
-        yx += S[S_NW] * (T)x1W.x + S[S_NW + 1] * (T)x1W.y;
-        yy += S[S_NW + 2] * (T)x1W.x + S[S_NW + 3] * (T)x1W.y;
-        yx += eWp[0] * (T)x1pW.x + eWp[2] * (T)x1pW.y;
-        yy += eWp[1] * (T)x1pW.x + eWp[3] * (T)x1pW.y;
+        yx = fma(S[S_D], (T)x1p.x, yx);
+        yx = fma(S[S_D + 1], (T)x1p.y, yx);
+        yy = fma(S[S_D + 1], (T)x1p.x, yy);
+        yy = fma(S[S_D + 2], (T)x1p.y, yy);
+        yx = fma(S[S_E], (T)x1pE.x, yx);
+        yx = fma(S[S_E + 1], (T)x1pE.y, yx);
+        yy = fma(S[S_E + 2], (T)x1pE.x, yy);
+        yy = fma(S[S_E + 3], (T)x1pE.y, yy);
+        yx = fma(S[S_N], (T)x1c.x, yx);
+        yx = fma(S[S_N + 1], (T)x1c.y, yx);
+        yy = fma(S[S_N + 2], (T)x1c.x, yy);
+        yy = fma(S[S_N + 3], (T)x1c.y, yy);
+        yx = fma(S[S_NE], (T)x1E.x, yx);
+        yx = fma(S[S_NE + 1], (T)x1E.y, yx);
+        yy = fma(S[S_NE + 2], (T)x1E.x, yy);
+        yy = fma(S[S_NE + 3], (T)x1E.y, yy);
+        yx = fma(S[S_NW], (T)x1W.x, yx);
+        yx = fma(S[S_NW + 1], (T)x1W.y, yx);
+        yy = fma(S[S_NW + 2], (T)x1W.x, yy);
+        yy = fma(S[S_NW + 3], (T)x1W.y, yy);
+        yx = fma(eWp[0], (T)x1pW.x, yx);
+        yx = fma(eWp[2], (T)x1pW.y, yx);
+        yy = fma(eWp[1], (T)x1pW.x, yy);
+        yy = fma(eWp[3], (T)x1pW.y, yy);
         if constexpr (kPower) {
           x2[np] = mk2<TV>(P.inv[0] * yx + P.inv[1] * yy, P.inv[1] * yx + P.inv[2] * yy);
         } else {
