@@ -114,6 +114,12 @@ class NestedDissection:
         K = sp.csr_matrix(K)
         if K.shape != (self.n, self.n):
             raise ValueError("matrix is %s, grid needs %d dofs" % (K.shape, self.n))
+        # one line of nodes separates only if no entry couples nodes further apart
+        # than the eight neighbours (true for Q1, not for Q2 elements)
+        rn = np.repeat(np.arange(self.n), np.diff(K.indptr)) // 2
+        cn = K.indices // 2
+        if np.any(np.abs(rn % self.m - cn % self.m) > 1) or np.any(np.abs(rn // self.m - cn // self.m) > 1):
+            raise ValueError("the matrix couples nodes beyond the eight-neighbour stencil")
         pos = np.full(self.n, -1, dtype=np.int64)
         updates: dict[int, np.ndarray] = {}
         # a front is "big" if it or any front below it is; the small subtrees

@@ -86,6 +86,8 @@ def newton(prob, tol=1e-10, method="svn", max_newton=200, max_halvings=30,
     ``step`` may pass a prepared ``Step`` (e.g. with a manufactured source in
     the atmospheric-stress slot)."""
     st = Step(prob) if step is None else step
+    if solve is direct_solve:
+        solve = getattr(st, "direct_solver", direct_solve)
     m = st.mesh
     v = m.zero_boundary(prob.v_old if v0 is None else v0)
     pi = None

@@ -10,11 +10,11 @@ Layouts (the same as the C-ABI):
     index [j, i, k] with k = 0 (x) / 1 (y), node (i, j) at (i*dx, j*dx).
 """
 from .fields import (Constants, Problem, gaussian_random_field, ice_fields,
-                     rankine_vortex, ocean_gyre, make_problem, config,
+                     rankine_vortex, ocean_gyre, make_problem, make_problem_q2, config,
                      translating_centre, vortex_centre, problem_one, problem_two,
                      problem_two_wind, problem_two_ocean, CONFIG_NAMES)
 
 __all__ = ["Constants", "Problem", "gaussian_random_field", "ice_fields",
-           "rankine_vortex", "ocean_gyre", "make_problem", "config",
+           "rankine_vortex", "ocean_gyre", "make_problem", "make_problem_q2", "config",
            "translating_centre", "vortex_centre", "problem_one", "problem_two",
            "problem_two_wind", "problem_two_ocean", "CONFIG_NAMES"]

@@ -133,6 +133,20 @@ def make_problem(N: int, seed: int, L: float = 512e3, const: Constants | None = 
                    v_old=vo, dt=dt)
 
 
+def make_problem_q2(N: int, seed: int, L: float = 512e3, const: Constants | None = None,
+                    dt: float = 1800.0, centre=None, v_old=None) -> Problem:
+    """The standard synthetic step for Q2 velocity elements on N x N cells: the
+    same cell fields as ``make_problem(N, seed)``, the node fields on the
+    (2N+1)^2 Q2 nodes (spacing L / 2N)."""
+    const = const or Constants()
+    h, A = ice_fields(N, L, seed)
+    c = centre if centre is not None else vortex_centre(L, seed + 2)
+    wind = rankine_vortex(2 * N, L, c)
+    ocean = ocean_gyre(2 * N, L)
+    vo = np.zeros((2 * N + 1, 2 * N + 1, 2)) if v_old is None else np.array(v_old, dtype=np.float64)
+    return Problem(N=N, L=L, const=const, h=h, A=A, wind=wind, ocean=ocean, v_old=vo, dt=dt)
+
+
 def translating_centre(L: float, seed: int, t: float, speed: float = 10.0):
     """Vortex centre at time t for the translating-vortex trajectory."""
     c0 = vortex_centre(L, seed + 2, 0.2, 0.35)
