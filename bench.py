@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip training / using the learned initial guess")
     ap.add_argument("--learned-traj", type=int, default=64)
     ap.add_argument("--learned-epochs", type=int, default=25)
+    ap.add_argument("--learned-c4", action="store_true",
+                    help="learned-start study: train on 2000 solver pairs at 256^2, test at 256^2 and 1024^2")
     return ap.parse_args()
 
 
@@ -186,6 +188,7 @@ FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 20
 # 1,057,800 padded nodes); set to None whenever that kernel changes until it is
 # captured again.
 SWEEP_TRAFFIC_PER_NODE = (140.884992e6 + 8.641024e6) / 1_057_800
+SWEEP_TRAFFIC_SOURCE = "ncu capture at 1024^2 scaled by nodes (profiles/k_cheb_sweep2s_fp32_1024.md)"
 
 
 def sweep_bytes_per_node(mixed: bool, fp32_coef: bool) -> int:
@@ -195,6 +198,36 @@ def sweep_bytes_per_node(mixed: bool, fp32_coef: bool) -> int:
     if not mixed:
         return 19 * 8 + 3 * 8 + 16 * 5
     return 19 * (4 if fp32_coef else 2) + 3 * 4 + 8 * 5
+
+
+def vcycle_bytes(N: int, degree: int = 6, coarse_N: int = 4, stream_min_N: int = 1024) -> float:
+    """Algorithmic HBM bytes of one FP32 V-cycle over every level (mixed path, FP32
+    stencils), following the V-cycle's launch sequence: per level with N cells and
+    n = (N+1)^2 nodes, pre-smoothing from zero (a two-step pass without x0, d0 reads,
+    112 B/node, where the streaming or TMA kernel runs; else a pointwise first step,
+    36 B/node, plus a single step), two-step passes (128 B/node) and single steps
+    (128 B/node) for the rest of the degree, the post-smoothing passes, the residual
+    (19 stencil values + x + b read, r written: 100 B/node), restriction (r read, 8 B
+    per fine node) and prolongation-add (x read and written, 16 B per fine node,
+    coarse reads counted at the coarse level's 8 B/node); the dense coarsest solve
+    is counted as its matrix read."""
+    total, n_lev = 0.0, N
+    while n_lev > coarse_N:
+        nodes = (n_lev + 1) ** 2
+        pre_rest = degree
+        if degree >= 2 and n_lev >= stream_min_N:
+            b = 112.0
+            pre_rest -= 2
+        else:
+            b = 36.0
+            pre_rest -= 1
+        b += 128.0 * (pre_rest // 2 + pre_rest % 2)       # pairs, then one single step
+        b += 128.0 * (degree // 2 + degree % 2)           # post-smoothing
+        b += 100.0 + 8.0 + 16.0 + 8.0                    # residual, restrict, prolong-add, coarse read
+        total += b * nodes
+        n_lev //= 2
+    m = 2 * (n_lev - 1) ** 2
+    return total + 8.0 * m * m
 
 
 def rel_l2(a, b) -> float:
@@ -394,8 +427,18 @@ def run_ours(args, rank, world):
                     "frac": ach / hbm_peak,
                     "traffic": (SWEEP_TRAFFIC_PER_NODE * (N + 1) * ((N + 1 + 7) // 8 * 8)
                                 if (mixed and SWEEP_TRAFFIC_PER_NODE) else None),
-                    "traffic_source": "ncu capture at 1024^2 scaled by nodes (profiles/k_cheb_sweep2s_fp32_1024.md)",
+                    "traffic_source": SWEEP_TRAFFIC_SOURCE,
                     "launches": n, "avg_us": avg_s * 1e6, "algorithmic_bytes_per_launch": byt}
+        roof_vc = None
+        ms, n = prof["vcycle"]
+        if n and mixed:
+            byt = vcycle_bytes(N, SETTINGS["cheb_degree"], SETTINGS["coarse_N"])
+            avg_s = ms / 1000.0 / n
+            roof_vc = {"kernel": "whole FP32 V-cycle (every level: sweeps incl. zero-start passes, residual, "
+                                 "transfers, coarse solve; one CUDA graph launch)", "bound": "hbm",
+                       "achieved": byt / avg_s / 1e9, "peak": hbm_peak, "peak_source": peak_src, "unit": "GB/s",
+                       "frac": byt / avg_s / 1e9 / hbm_peak, "avg_us": avg_s * 1e6, "launches": n,
+                       "algorithmic_bytes_per_launch": byt}
         roof64 = None
         ms, n = prof["apply"]
         if n:
@@ -420,6 +463,7 @@ def run_ours(args, rank, world):
             "krylov_per_newton": stats[0]["krylov_per_newton"],
             "alpha_hist": stats[0]["alpha_hist"],
             "gpu_launches": int(launches), "clocks": clk, "roofline": roof, "roofline_fp64_apply": roof64,
+            "roofline_vcycle": roof_vc,
             "kernel_share": shares, "dominant_kernel_class": dom, "e2e": e2e, "fp64_path": fp64,
             "learned": (dict(learned_info, used=[st["learned_used"] for st in stats],
                              fallback=[st["learned_fallback"] for st in stats],
@@ -479,6 +523,84 @@ def run_ensemble(args):
             "sequential_s": t_seq, "batch_s": t_batch, "speedup_vs_sequential": t_seq / t_batch,
             "newton_iters_mean": float(np.mean([x["newton_iters"] for x in st])),
             "krylov_iters_mean": float(np.mean([x["krylov_iters_total"] for x in st]))}
+
+
+def run_learned_c4(args):
+    """Learned initial guess on its own workload: 200 translating-vortex trajectories
+    x 10 steps at 256^2 (2000 solver-generated pairs, seeds 10000+) train the network;
+    held-out trajectories (seeds 20000+) at 256^2 and 1024^2 are then solved from
+    the same v^n without the network and with each acceptance rule, inside the
+    mixed solver of the timed workload; Newton / Krylov iterations saved and the
+    fallback rate are reported per rule."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2204_10822_gb300 import Solver
+    from paper_2204_10822_gb300.learned import Net, generate_pairs, he_init, train
+
+    kw = dict(SETTINGS, precision="mixed", vcycle_fp32=1)
+    t0 = time.perf_counter()
+    pairs, _ = generate_pairs(256, n_traj=200, steps=10, seed0=10000, **kw)
+    t_gen = time.perf_counter() - t0
+    net = Net(G=256, batch=8)
+    net.set_params(he_init(0, net.nparam))
+    t0 = time.perf_counter()
+    losses = train(net, pairs, epochs=args.learned_epochs, lr=2e-3)
+    torch.cuda.synchronize()
+    t_train = time.perf_counter() - t0
+    n_pairs = len(pairs)
+    del pairs
+    torch.cuda.empty_cache()
+    rules = {"off": None, "residual": 0, "energy": 1, "blend": 3, "always": 2, "always_pi_old": 4}
+    out = {"pairs": n_pairs, "train_steps": len(losses), "epochs": args.learned_epochs,
+           "loss_first": float(np.mean(losses[:10])), "loss_last": float(np.mean(losses[-10:])),
+           "generate_s": t_gen, "train_s": t_train, "tests": {}}
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    L, dt = 512e3, 1800.0
+    for N, n_traj, steps in ((256, 10, 10), (1024, 3, 6)):
+        solvers = {}
+        for name, rule in rules.items():
+            solvers[name] = Solver(N, L, **dict(kw, learned_rule=rule or 0))
+            if rule is not None:
+                net.attach(solvers[name], True)
+        rec = {name: {"newton": [], "krylov": [], "fallback": [], "alpha": []} for name in rules}
+        ocean = t(W.ocean_gyre(N, L))
+        for k in range(n_traj):
+            seed = 20000 + k
+            h, A = W.ice_fields(N, L, seed)
+            hd, Ad = t(h), t(A)
+            v = torch.zeros((N + 1, N + 1, 2), dtype=torch.float64, device="cuda")
+            for n in range(steps):
+                wind = t(W.rankine_vortex(N, L, W.translating_centre(L, seed, (n + 1) * dt)))
+                nxt = None
+                for name, s in solvers.items():
+                    s.set_forcing(hd, Ad, wind, ocean, v)
+                    vn, st = s.step(dt, args.tol, raise_on_error=False)
+                    r = rec[name]
+                    r["newton"].append(st["newton_iters"])
+                    r["krylov"].append(st["krylov_iters_total"])
+                    r["fallback"].append(st["learned_fallback"])
+                    r["alpha"].append(st["learned_alpha"])
+                    if name == "off":
+                        nxt = vn.clone()
+                v = nxt
+        base_n, base_k = np.mean(rec["off"]["newton"]), np.mean(rec["off"]["krylov"])
+        res = {"trajectories": n_traj, "steps": steps, "off": {"newton_mean": base_n, "krylov_mean": base_k}}
+        for name in ("residual", "energy", "blend", "always", "always_pi_old"):
+            r = rec[name]
+            res[name] = {"newton_mean": float(np.mean(r["newton"])), "krylov_mean": float(np.mean(r["krylov"])),
+                         "newton_saved_per_step": float(base_n - np.mean(r["newton"])),
+                         "krylov_saved_per_step": float(base_k - np.mean(r["krylov"])),
+                         "fallback_rate": float(np.mean(r["fallback"])),
+                         "alpha_mean": float(np.mean(r["alpha"]))}
+        out["tests"]["%dx%d" % (N, N)] = res
+        for s in solvers.values():
+            s.close()
+    return {"metric": "learned-start Newton iterations saved per step", "unit": "Newton iterations",
+            "value": out["tests"]["256x256"]["blend"]["newton_saved_per_step"], "higher_is_better": True,
+            "data": "synthetic (solver-generated pairs)", "n_gpus": 1,
+            "config": {"workload": "learned start: train 2000 pairs at 256^2, test 256^2 and 1024^2"}, **out}
 
 
 def run_problem_two(args):
@@ -542,6 +664,9 @@ def main():
         return 0
     if args.problem2:
         print(json.dumps(run_problem_two(args)))
+        return 0
+    if args.learned_c4:
+        print(json.dumps(run_learned_c4(args)))
         return 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

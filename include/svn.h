@@ -97,7 +97,11 @@ typedef struct svn_params {
   double lmax_safety;       /* the estimate is multiplied by this factor */
   int learned_rule;         /* acceptance of the learned guess v_p: 0 (default) keep it if
                                ||R(v_p)|| < ||R(v_old)||; 1 if Phi(v_p) < Phi(v_old);
-                               2 always */
+                               2 always; 3 blend: start from v_old + alpha (v_p - v_old)
+                               with the alpha in {1, 1/2, ..., 1/64} of lowest Phi, if
+                               that is below Phi(v_old) (Phi is convex, so the blend is
+                               never worse than v_old in energy); 4 always, with the dual
+                               state pi_0 = tau(v_old)/Delta(v_old) of the plain start */
   int method;               /* 0 (default): stress-velocity Newton (Section 4.2);
                                1: standard Newton (Section 4.1, Eq. "standardNewton"),
                                i.e. the same operator with pi = tau(v)/Delta(v) at
@@ -105,11 +109,13 @@ typedef struct svn_params {
   int mg_rebuild;           /* rebuild the V-cycle hierarchy (Galerkin levels, smoother
                                data) every mg_rebuild Newton iterations (1 = always);
                                the FP64 outer operator is rebuilt every iteration */
-  int cheb_fuse;            /* 1 (default): two Chebyshev steps per pass (row-streaming
-                               warps on levels with N >= 1024 in FP32, a shared-memory
-                               tile with a one-node ring elsewhere); 2: two steps per
-                               pass, tile kernel on every level; 3: two steps per pass,
-                               row-streaming on every FP32 level; 0: one step per pass */
+  int cheb_fuse;            /* two Chebyshev steps per pass, kernel per level: 1 (default)
+                               row-streaming warps on FP32 levels with N >= 1024 and a
+                               shared-memory tile with a one-node ring elsewhere; 2: the
+                               shared-memory tile on every level; 3: row-streaming warps
+                               on every FP32 level; 4: TMA-staged CTA tiles on FP32-stencil
+                               levels with N >= 1024, tile elsewhere; 5: TMA-staged on
+                               every FP32-stencil level; 0: one step per pass */
   int fused_trial;          /* 1 (default): evaluate Phi, R and pi at the unit step in one
                                fused pass; 0: separate energy / residual / dual passes */
   int vcycle_fp32;          /* mixed precision: 1 (default) stores the V-cycle stencils
@@ -125,6 +131,11 @@ typedef struct svn_params {
                                above krylov_rtol, the Newton direction is recomputed
                                with a 100x tighter tolerance (at most 3 times per
                                Newton iteration).  Default 1/64; 0 disables it */
+  int wait_polls;           /* bound of every mbarrier wait of the TMA-staged sweep, in
+                               non-blocking polls (0: default 2^22).  A wait that runs
+                               out abandons its block's work; the step then fails with
+                               SVN_ERR_TIMEOUT (checked after each linearisation and
+                               each Krylov solve; the counter is device-wide) */
 } svn_params;
 
 typedef struct svn_stats {
@@ -142,6 +153,7 @@ typedef struct svn_stats {
   double res_hist[SVN_MAX_NEWTON + 1];
   double alpha_hist[SVN_MAX_NEWTON];
   int direction_retries;    /* Newton directions recomputed by the retry_alpha safeguard */
+  double learned_alpha;     /* weight of the learned guess in the start (0: not used) */
 } svn_stats;
 
 typedef struct svn_handle svn_handle;

@@ -36,7 +36,7 @@ class SvnParams(ctypes.Structure):
         ("fused_trial", c_int),
         ("vcycle_fp32", c_int),
         ("cheb_degree_coarse", c_int),
-        ("retry_alpha", c_double)]
+        ("retry_alpha", c_double), ("wait_polls", c_int)]
 
 
 class SvnStats(ctypes.Structure):
@@ -46,7 +46,7 @@ class SvnStats(ctypes.Structure):
                 ("krylov_per_newton", c_int * SVN_MAX_NEWTON),
                 ("res_hist", c_double * (SVN_MAX_NEWTON + 1)),
                 ("alpha_hist", c_double * SVN_MAX_NEWTON),
-                ("direction_retries", c_int)]
+                ("direction_retries", c_int), ("learned_alpha", c_double)]
 
     def to_dict(self) -> dict:
         n = self.newton_iters
@@ -56,7 +56,7 @@ class SvnStats(ctypes.Structure):
                 "res0": self.res0, "res_final": self.res_final, "rel_res_final": self.rel_res_final,
                 "seconds": self.seconds, "krylov_per_newton": list(self.krylov_per_newton[:n]),
                 "res_hist": list(self.res_hist[:n + 1]), "alpha_hist": list(self.alpha_hist[:n]),
-                "direction_retries": self.direction_retries}
+                "direction_retries": self.direction_retries, "learned_alpha": self.learned_alpha}
 
 
 _SIGS = {

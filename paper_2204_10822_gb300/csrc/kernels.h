@@ -45,6 +45,36 @@ void launch_trial(cudaStream_t s, const Layout& g, const Phys& ph, const double2
                   const double* P, const double* rhoH, const double* fq, const double* voq, const double* pi,
                   double* pi_t, double* eb, double2* R, double* partial_e, double* out_e, double* partial_r);
 
+// Final compensated reduction of per-block energy partials (layout of launch_energy).
+void launch_energy_final(cudaStream_t s, int k, const double* partial, int nblocks, double* out);
+
+// ---- Q2 velocity elements (q2_kernels.cu) ----
+// N x N cells (cell c = j N + i), nodes of the (2N+1)^2 grid in the node layout gq
+// (= make_layout(2N, L)); quadrature planes of cpl entries (9 points per cell).
+struct Q2Geom {
+  int N;
+  long long cpl;
+  Layout gq;
+};
+int q2_init_tables();   // basis tables into constant memory of the current device
+void launch_q2_precompute(cudaStream_t s, const Q2Geom& q, double dt, const PhysConst& pc, const double* hcell,
+                          const double* A, const double* wind, const double* ocean, const double* vold, double* P,
+                          double* rhoH, double* fq, double* voq);
+void launch_q2_pi_init(cudaStream_t s, const Q2Geom& q, const Phys& ph, const double2* v, double* pi);
+int q2_node_partials(const Q2Geom& q);
+void launch_q2_residual(cudaStream_t s, const Q2Geom& q, const Phys& ph, const double2* v, const double* P,
+                        const double* rhoH, const double* fq, const double* voq, double* eb, double2* R,
+                        double* partial);
+int q2_energy_partials(const Q2Geom& q);
+void launch_q2_energy(cudaStream_t s, const Q2Geom& q, const Phys& ph, int k, const AlphaSet& al, const double2* v,
+                      const double2* dv, const double* P, const double* rhoH, const double* fq, const double* voq,
+                      double* partial, double* out);
+void launch_q2_element_matrices(cudaStream_t s, const Q2Geom& q, const Phys& ph, const double2* v, const double* pi,
+                                const double* P, const double* rhoH, const double* voq, double* ke);
+void launch_q2_apply(cudaStream_t s, const Q2Geom& q, const double* ke, const double2* x, double* eb, double2* y);
+void launch_q2_dual_update(cudaStream_t s, const Q2Geom& q, const Phys& ph, double alpha, const double2* v,
+                           const double2* dv, double* pi);
+
 // ---- transport of A and H (transport.cu) ----
 int transport_courant_blocks(int N);
 // per-block maxima of the outflow Courant number (dt_dx * outflow) into partial
@@ -69,7 +99,7 @@ void launch_max_final(cudaStream_t s, const double* partial, int n, double* out)
 // launch_cheb_sweep2 (two steps per row-streaming pass where it applies).
 template <typename TS, typename TD, typename TV>
 void launch_power_lmax(cudaStream_t s, const Layout& g, const TS* st, const TD* dinv, int iters, double safety,
-                       TV* x0, TV* x1, double* partial, double* lmax, int stream);
+                       TV* x0, TV* x1, double* partial, double* lmax, int stream, unsigned polls = 0);
 // Chebyshev smoothing (Saad Alg. 12.1 on D^-1 A over [lo lmax, lmax]); the
 // step coefficients are computed on the device from lmax (launch_cheb_coefs).
 template <typename T>
@@ -84,10 +114,21 @@ void launch_cheb_sweep(cudaStream_t s, const Layout& g, const TS* st, const TD* 
 // Steps (step, step + 1) fused; x0 != x2 and d0 != d2.  stream: 1 = the
 // row-streaming kernel on FP32 levels with N >= 1024, the shared-memory tile
 // kernel elsewhere; 2 = row-streaming on every FP32 level; 0 = tile kernel.
+// 3 = the TMA-staged kernel (sweep_tma.cu) on every level with an FP32 stencil,
+// 4 = the TMA-staged kernel on FP32-stencil levels with N >= 1024 (tile kernel
+// below); polls bounds each of its mbarrier waits (0: default).
 template <typename TS, typename TD, typename TV>
 void launch_cheb_sweep2(cudaStream_t s, const Layout& g, const TS* st, const TD* dinv,
                         const typename ScalarOf<TV>::type* coef, int step, const TV* x0, TV* x2, const TV* d0,
-                        TV* d2, const TV* b, int stream);
+                        TV* d2, const TV* b, int stream, unsigned polls = 0);
+// TMA-staged two-step sweep on an FP32 level (power: x2 = (D^-1 A)^2 x0);
+// false when it cannot run (no tensor-map entry point), nothing launched then.
+bool launch_cheb_sweep2_tma(cudaStream_t s, const Layout& g, const float* st, const float* dinv, const float* coef,
+                            int step, const float2* x0, float2* x2, const float2* d0, float2* d2, const float2* b,
+                            bool power, unsigned polls);
+// Number of TMA-sweep CTAs whose bounded wait gave up since the last reset
+// (device-wide counter; -1 on a CUDA error).  pinned: one host-pinned unsigned.
+int sweep_tma_timeouts(cudaStream_t s, unsigned* pinned, bool reset);
 // Whether launch_cheb_sweep2 takes the row-streaming kernel on level g for
 // FP32 vectors; only that kernel accepts x0 = d0 = NULL (start from zero).
 bool sweep2_streams(const Layout& g, int stream);

@@ -7,6 +7,7 @@
 // Jacobi storage, TV = vector type (double2 / float2); arithmetic in the
 // vector's scalar type.
 #include <algorithm>
+#include <type_traits>
 
 #include "kernels.h"
 
@@ -847,7 +848,12 @@ static int stream_resident_warps() {
   }();
   return w;
 }
-bool sweep2_streams(const Layout& g, int stream) { return stream == 2 || (stream == 1 && g.N >= kStreamMinN); }
+bool sweep2_streams(const Layout& g, int stream) {
+  return stream == 2 || stream == 3 || ((stream == 1 || stream == 4) && g.N >= kStreamMinN);
+}
+static inline bool sweep2_tma(const Layout& g, int stream) {
+  return stream == 3 || (stream == 4 && g.N >= kStreamMinN);
+}
 
 static inline int stream_rows(const Layout& g, int resident_warps) {
   const int nstrips = (g.n1 + kStreamCols - 1) / kStreamCols;
@@ -885,7 +891,7 @@ int launch_dinv_gershgorin(cudaStream_t s, const Layout& g, const TS* st, TD* di
 
 template <typename TS, typename TD, typename TV>
 void launch_power_lmax(cudaStream_t s, const Layout& g, const TS* st, const TD* dinv, int iters, double safety,
-                       TV* x0, TV* x1, double* partial, double* lmax, int stream) {
+                       TV* x0, TV* x1, double* partial, double* lmax, int stream, unsigned polls) {
   note_launch();
   k_checkerboard<TV><<<ngrid(g), kBlk, 0, s>>>(g, x0);
   TV* a = x0;
@@ -900,9 +906,15 @@ void launch_power_lmax(cudaStream_t s, const Layout& g, const TS* st, const TD* 
       const int chunks = (g.n1 + rows - 1) / rows;
       const unsigned blocks = (unsigned)(((long long)nstrips * chunks * 32 + 127) / 128);
       for (; iters - k > 2; k += 2) {
-        note_launch();
-        k_cheb_sweep2s<TS, TD, TV, true><<<blocks, 128, 0, s>>>(g, st, dinv, nullptr, 0, a, b, nullptr, nullptr,
-                                                                 nullptr, rows);
+        bool done = false;
+        if constexpr (std::is_same<TS, float>::value)
+          if (sweep2_tma(g, stream))
+            done = launch_cheb_sweep2_tma(s, g, st, dinv, nullptr, 0, a, b, nullptr, nullptr, nullptr, true, polls);
+        if (!done) {
+          note_launch();
+          k_cheb_sweep2s<TS, TD, TV, true><<<blocks, 128, 0, s>>>(g, st, dinv, nullptr, 0, a, b, nullptr, nullptr,
+                                                                   nullptr, rows);
+        }
         TV* t = a;
         a = b;
         b = t;
@@ -927,12 +939,13 @@ void launch_power_lmax(cudaStream_t s, const Layout& g, const TS* st, const TD* 
   k_lmax_from_norms<<<1, 1024, 0, s>>>(partial, partial + nb, (int)nb, safety, lmax);
 }
 template void launch_power_lmax<double, double, double2>(cudaStream_t, const Layout&, const double*, const double*,
-                                                         int, double, double2*, double2*, double*, double*, int);
+                                                         int, double, double2*, double2*, double*, double*, int,
+                                                         unsigned);
 template void launch_power_lmax<float, float, float2>(cudaStream_t, const Layout&, const float*, const float*, int,
-                                                       double, float2*, float2*, double*, double*, int);
+                                                       double, float2*, float2*, double*, double*, int, unsigned);
 template void launch_power_lmax<__nv_bfloat16, float, float2>(cudaStream_t, const Layout&, const __nv_bfloat16*,
                                                               const float*, int, double, float2*, float2*, double*,
-                                                              double*, int);
+                                                              double*, int, unsigned);
 
 void launch_max_final(cudaStream_t s, const double* partial, int n, double* out) {
   note_launch();
@@ -965,7 +978,12 @@ void launch_cheb_sweep(cudaStream_t s, const Layout& g, const TS* st, const TD* 
 template <typename TS, typename TD, typename TV>
 void launch_cheb_sweep2(cudaStream_t s, const Layout& g, const TS* st, const TD* dinv,
                         const typename ScalarOf<TV>::type* coef, int step, const TV* x0, TV* x2, const TV* d0,
-                        TV* d2, const TV* b, int stream) {
+                        TV* d2, const TV* b, int stream, unsigned polls) {
+  if constexpr (std::is_same<TS, float>::value) {
+    if (sweep2_tma(g, stream) &&
+        launch_cheb_sweep2_tma(s, g, st, dinv, coef, step, x0, x2, d0, d2, b, false, polls))
+      return;
+  }
   note_launch();
   if constexpr (sizeof(typename ScalarOf<TV>::type) == 4) {
     if (sweep2_streams(g, stream)) {
@@ -1041,7 +1059,7 @@ void launch_convert_stencil(cudaStream_t s, const Layout& g, const TA* a, TB* b)
   template void launch_coarse_dense<TS>(cudaStream_t, const Layout&, const TS*, double*);                       \
   template void launch_cheb_sweep2<TS, TD, TV>(cudaStream_t, const Layout&, const TS*, const TD*,                \
                                                const typename ScalarOf<TV>::type*, int, const TV*, TV*,          \
-                                               const TV*, TV*, const TV*, int);
+                                               const TV*, TV*, const TV*, int, unsigned);
 
 SVN_INST_LEVEL(double, double, double2)
 SVN_INST_LEVEL(__nv_bfloat16, float, float2)

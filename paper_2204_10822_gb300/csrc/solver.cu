@@ -281,9 +281,30 @@ int energy(svn_handle* h, const double2* v, const double2* dv, const double* alp
   return SVN_OK;
 }
 
+// Two-step sweep kernel of launch_cheb_sweep2 for the cheb_fuse setting.
+inline int sweep_mode(const svn_params& p) {
+  switch (p.cheb_fuse) {
+    case 1: return 1;   // row-streaming kernel on the FP32 levels with N >= 1024, tile kernel below
+    case 3: return 2;   // row-streaming kernel on every FP32 level
+    case 4: return 4;   // TMA-staged kernel on the FP32-stencil levels with N >= 1024
+    case 5: return 3;   // TMA-staged kernel on every FP32-stencil level
+    default: return 0;  // shared-memory tile kernel
+  }
+}
+
 // Chebyshev degree used on multigrid level l
 inline int level_degree(const svn_params& p, int l) {
   return (l > 0 && p.cheb_degree_coarse > 0) ? p.cheb_degree_coarse : p.cheb_degree;
+}
+
+// SVN_ERR_TIMEOUT if a TMA-staged sweep gave up waiting for its copies since the last check.
+int check_sweep_timeouts(svn_handle* h) {
+  unsigned* pinned = reinterpret_cast<unsigned*>(h->hostbuf + h->hostbuf_len - 1);
+  const int n = sweep_tma_timeouts(h->stream, pinned, true);
+  if (n < 0) return fail(h, SVN_ERR_CUDA, "reading the sweep timeout counter failed");
+  if (n > 0)
+    return fail(h, SVN_ERR_TIMEOUT, "%d multigrid sweep blocks gave up waiting for their TMA copies", n);
+  return SVN_OK;
 }
 
 int linearize(svn_handle* h, const double2* v, const double* pi, bool hierarchy = true) {
@@ -302,7 +323,7 @@ int linearize(svn_handle* h, const double2* v, const double* pi, bool hierarchy 
     launch_rap<double, double>(s, h->lv[l - 1].g, h->lv[l].g, h->lv[l - 1].st64, h->lv[l].st64);
   }
   CKL();
-  const int smode = h->prm.cheb_fuse == 1 ? 1 : h->prm.cheb_fuse == 3 ? 2 : 0;   // two-step kernel choice
+  const int smode = sweep_mode(h->prm);   // two-step kernel choice
   for (int l = 0; l < L - 1; ++l) {
     Level& lv = h->lv[l];
     int nb;
@@ -322,11 +343,11 @@ int linearize(svn_handle* h, const double2* v, const double* pi, bool hierarchy 
       if (h->mixed && h->prm.vcycle_fp32)
         launch_power_lmax<float, float, float2>(s, lv.g, lv.st32, (const float*)lv.dinv, h->prm.lmax_iters,
                                                 h->prm.lmax_safety, (float2*)lv.x[0], (float2*)lv.x[1], h->partial,
-                                                lv.lmax, smode);
+                                                lv.lmax, smode, (unsigned)h->prm.wait_polls);
       else if (h->mixed)
         launch_power_lmax<__nv_bfloat16, float, float2>(s, lv.g, lv.st16, (const float*)lv.dinv, h->prm.lmax_iters,
                                                         h->prm.lmax_safety, (float2*)lv.x[0], (float2*)lv.x[1],
-                                                        h->partial, lv.lmax, smode);
+                                                        h->partial, lv.lmax, smode, (unsigned)h->prm.wait_polls);
       else
         launch_power_lmax<double, double, double2>(s, lv.g, lv.st64, (const double*)lv.dinv, h->prm.lmax_iters,
                                                    h->prm.lmax_safety, (double2*)lv.x[0], (double2*)lv.x[1],
@@ -347,7 +368,7 @@ int linearize(svn_handle* h, const double2* v, const double* pi, bool hierarchy 
   CK(cudaStreamSynchronize(s));
   memcpy(&info, h->hostbuf, sizeof(int));
   if (info != 0) return fail(h, SVN_ERR_ARG, "coarsest operator is not positive definite (pivot %d)", info);
-  return SVN_OK;
+  return check_sweep_timeouts(h);
 }
 
 // Times level-0 Chebyshev sweeps: CUDA events around the launch, either as
@@ -413,7 +434,7 @@ void vcycle(svn_handle* h, int l, const TV* b, TV* xout) {
   TV* dalt = (TV*)lv.d2;
   TV* cur = x0;
   const bool fuse = h->prm.cheb_fuse != 0;
-  const int smode = h->prm.cheb_fuse == 1 ? 1 : h->prm.cheb_fuse == 3 ? 2 : 0;   // two-step kernel choice
+  const int smode = sweep_mode(h->prm);   // two-step kernel choice
   // Chebyshev steps [k, kend) from cur; the result lands in `last_dst` when given
   auto smooth = [&](int k, int kend, TV* last_dst) {
     while (k < kend) {
@@ -422,7 +443,8 @@ void vcycle(svn_handle* h, int l, const TV* b, TV* xout) {
       TV* dst = (last && last_dst && last_dst != cur) ? last_dst : (cur == x0 ? x1 : x0);
       SweepTimer tm(h, l, pair ? 2 : 1);
       if (pair) {
-        launch_cheb_sweep2<TS, TD, TV>(s, lv.g, st, dinv, coef, k, cur, dst, d, dalt, b, smode);
+        launch_cheb_sweep2<TS, TD, TV>(s, lv.g, st, dinv, coef, k, cur, dst, d, dalt, b, smode,
+                                       (unsigned)h->prm.wait_polls);
         std::swap(d, dalt);
         k += 2;
       } else {
@@ -435,7 +457,8 @@ void vcycle(svn_handle* h, int l, const TV* b, TV* xout) {
   // pre-smoothing from x = 0: steps 0 and 1 in one streaming pass where that
   // kernel runs, else step 0 pointwise
   if (fuse && deg >= 2 && sizeof(T) == 4 && sweep2_streams(lv.g, smode)) {
-    launch_cheb_sweep2<TS, TD, TV>(s, lv.g, st, dinv, coef, 0, nullptr, x0, nullptr, d, b, smode);
+    launch_cheb_sweep2<TS, TD, TV>(s, lv.g, st, dinv, coef, 0, nullptr, x0, nullptr, d, b, smode,
+                                   (unsigned)h->prm.wait_polls);
     cur = x0;
     smooth(2, deg, nullptr);
   } else {
@@ -643,7 +666,7 @@ int fgmres(svn_handle* h, const double2* b, double2* x, double rtol, int maxit, 
     CKL();
   }
   *iters = total;
-  return SVN_OK;
+  return check_sweep_timeouts(h);
 }
 
 int check_params(svn_handle* h, const svn_params* p) {
@@ -658,8 +681,10 @@ int check_params(svn_handle* h, const svn_params* p) {
   if (p->coarse_N < 2 || p->coarse_N > 16) return fail(h, SVN_ERR_ARG, "coarse_N must be in [2, 16]");
   if (p->lmax_iters < 0 || p->lmax_iters > 60) return fail(h, SVN_ERR_ARG, "lmax_iters must be in [0, 60]");
   if (p->method != 0 && p->method != 1) return fail(h, SVN_ERR_ARG, "method must be 0 (svN) or 1 (stdN)");
+  if (p->learned_rule < 0 || p->learned_rule > 4) return fail(h, SVN_ERR_ARG, "learned_rule must be in [0, 4]");
   if (!(p->lmax_safety >= 1.0 && p->lmax_safety < 4.0)) return fail(h, SVN_ERR_ARG, "lmax_safety must be in [1, 4)");
-  if (p->cheb_fuse < 0 || p->cheb_fuse > 3) return fail(h, SVN_ERR_ARG, "cheb_fuse must be 0, 1, 2 or 3");
+  if (p->cheb_fuse < 0 || p->cheb_fuse > 5) return fail(h, SVN_ERR_ARG, "cheb_fuse must be in [0, 5]");
+  if (p->wait_polls < 0) return fail(h, SVN_ERR_ARG, "wait_polls must be >= 0");
   if (p->cheb_degree_coarse < 0 || p->cheb_degree_coarse > 16)
     return fail(h, SVN_ERR_ARG, "cheb_degree_coarse must be in [0, 16]");
   if (!(p->retry_alpha >= 0.0 && p->retry_alpha <= 1.0)) return fail(h, SVN_ERR_ARG, "retry_alpha must be in [0, 1]");
@@ -880,7 +905,30 @@ int step_impl(svn_handle* h, double dt, double tol, svn_stats* st) {
       net_predict_nodes(h->net, s, g, h->in_h, h->in_A, h->in_wind, h->in_ocean, h->in_vold, h->vt);
       CKL();
       bool take = false;
-      if (h->prm.learned_rule == 2) {
+      if (h->prm.learned_rule == 4) {
+        // the prediction as the velocity, the dual state of the plain start
+        launch_pi_init(s, g, ph, h->v, h->pi);
+        take = true;
+      } else if (h->prm.learned_rule == 3) {
+        // blend rule: v^n + alpha (v_pred - v^n) with the alpha in {1, 1/2, ..., 1/64}
+        // of lowest Phi (one multi-alpha energy pass), kept if it is below Phi(v^n)
+        launch_axpby_to(s, g, h->vt, -1.0, h->v, h->w);   // w = v_pred - v^n
+        CKL();
+        double al[MAX_ALPHA], phi[MAX_ALPHA];
+        al[0] = 0.0;
+        for (int a = 1; a < MAX_ALPHA; ++a) al[a] = std::ldexp(1.0, 1 - a);
+        TRY(energy(h, h->v, h->w, al, MAX_ALPHA, phi, nullptr));
+        int best = 0;
+        for (int a = 1; a < MAX_ALPHA; ++a)
+          if (std::isfinite(phi[a]) && phi[a] < phi[best]) best = a;
+        if (best > 0) {
+          launch_axpy(s, g, al[best], h->w, h->v);
+          CKL();
+          st->learned_alpha = al[best];
+        } else {
+          st->learned_fallback = 1;
+        }
+      } else if (h->prm.learned_rule == 2) {
         take = true;
       } else if (h->prm.learned_rule == 1) {
         // energy rule: keep the prediction if Phi(v_pred) < Phi(v^n)
@@ -894,12 +942,16 @@ int step_impl(svn_handle* h, double dt, double tol, svn_stats* st) {
         TRY(residual(h, h->vt, h->w, &rp));
         take = std::isfinite(rp) && rp < st->res0;
       }
-      if (take)
-        CK(cudaMemcpyAsync(h->v, h->vt, sizeof(double2) * g.plane, cudaMemcpyDeviceToDevice, s));
-      else
-        st->learned_fallback = 1;
+      if (h->prm.learned_rule != 3) {
+        if (take) {
+          CK(cudaMemcpyAsync(h->v, h->vt, sizeof(double2) * g.plane, cudaMemcpyDeviceToDevice, s));
+          st->learned_alpha = 1.0;
+        } else {
+          st->learned_fallback = 1;
+        }
+      }
     }
-    launch_pi_init(s, g, ph, h->v, h->pi);
+    if (!(st->learned_used && h->prm.learned_rule == 4)) launch_pi_init(s, g, ph, h->v, h->pi);
     CKL();
   }
   h->state_set = false;   // a later step restarts from its own v^n unless set_state is called again

@@ -30,7 +30,7 @@ def test_defaults_match_the_header():
     assert p.krylov_rtol == 1e-6 and p.restart == 30 and p.cheb_degree == 3 and p.coarse_N == 4
     assert p.precision == capi.SVN_FP64 and p.method == 0 and p.cheb_fuse == 1 and p.cheb_degree_coarse == 0
     assert p.lmax_iters == 15 and p.lmax_safety == 1.15 and p.use_graphs == 1 and p.vcycle_fp32 == 1
-    assert p.retry_alpha == 1.0 / 64.0
+    assert p.retry_alpha == 1.0 / 64.0 and p.wait_polls == 0
 
 
 def create(grid, params):
@@ -44,13 +44,14 @@ def create(grid, params):
 
 
 @pytest.mark.parametrize("field,value,needle", [
-    ("cheb_fuse", 4, "cheb_fuse"), ("method", 2, "method"), ("cheb_degree", 0, "cheb_degree"),
+    ("cheb_fuse", 6, "cheb_fuse"), ("wait_polls", -1, "wait_polls"), ("method", 2, "method"), ("cheb_degree", 0, "cheb_degree"),
     ("cheb_degree", 17, "cheb_degree"), ("restart", 0, "restart"), ("restart", 201, "restart"),
     ("cheb_degree_coarse", 17, "cheb_degree_coarse"), ("cheb_degree_coarse", -1, "cheb_degree_coarse"),
     ("lmax_safety", 0.5, "lmax_safety"), ("lmax_iters", 61, "lmax_iters"), ("cheb_lo", 1.0, "cheb_lo"),
     ("coarse_N", 1, "coarse_N"), ("precision", 7, "precision"), ("max_newton", 201, "max_newton"),
     ("max_halvings", -1, "max_halvings"), ("e", 0.0, "physical"), ("delta_min", 0.0, "physical"),
-    ("retry_alpha", -0.5, "retry_alpha"), ("retry_alpha", 2.0, "retry_alpha")])
+    ("retry_alpha", -0.5, "retry_alpha"), ("retry_alpha", 2.0, "retry_alpha"),
+    ("learned_rule", 5, "learned_rule"), ("learned_rule", -1, "learned_rule")])
 def test_bad_parameter_is_rejected(field, value, needle):
     p = defaults()
     setattr(p, field, value)

@@ -182,11 +182,11 @@ def test_vcycle_parity_level_degrees():
     assert relmax(z, zo) < 1e-9
 
 
-@pytest.mark.parametrize("fuse", [2, 3])
+@pytest.mark.parametrize("fuse", [2, 3, 5])
 def test_vcycle_parity_mixed_sweeps(fuse):
     # FP32 V-cycle (mixed precision) against the oracle's FP64 V-cycle, with the
-    # two-step sweeps done by the shared-memory tile kernel (cheb_fuse = 2) or
-    # by the row-streaming kernel on every level (cheb_fuse = 3); FP32
+    # two-step sweeps done by the shared-memory tile kernel (cheb_fuse = 2), the
+    # row-streaming kernel (3) or the TMA-staged kernel (5) on every level; FP32
     # rounding of the stencil and the arithmetic bounds the difference
     N = 64
     p = W.make_problem(N, seed=11)
@@ -204,18 +204,36 @@ def test_vcycle_parity_mixed_sweeps(fuse):
 
 @pytest.mark.parametrize("N", [1024, 2048])
 def test_streaming_sweep_matches_tile_sweep(N):
-    # at the sizes where the default takes the row-streaming kernel (finest
-    # levels, and its power mode for lambda_max) it computes the same V-cycle
-    # as the tile kernel up to FP32 summation order
+    # at the sizes where the row-streaming (default) and TMA-staged kernels run
+    # (finest levels, and their power mode for lambda_max) they compute the same
+    # V-cycle as the tile kernel up to FP32 summation order
     p = W.make_problem(N, seed=13)
     v = rand_v(N, 13)
     out = []
-    for fuse in (1, 2):
+    for fuse in (2, 1, 4):
         s = make_solver(p, precision="mixed", cheb_degree=6, cheb_lo=0.02, cheb_fuse=fuse)
         s.linearize(p.dt, dev(v), dev(np.zeros(s.pi_shape)))      # pi = 0 is a valid dual state
         out.append(host(s.precondition(dev(rand_v(N, 14, 1.0)))))
         s.close()
-    assert relmax(out[0], out[1]) < 1e-5, relmax(out[0], out[1])
+    assert relmax(out[1], out[0]) < 1e-5, relmax(out[1], out[0])
+    assert relmax(out[2], out[0]) < 1e-5, relmax(out[2], out[0])
+
+
+def test_sweep_wait_bound_reports_timeout():
+    # a one-poll bound makes every TMA-staged block give up at its first wait
+    # (the copies it just issued cannot have landed); the step must fail with
+    # SVN_ERR_TIMEOUT, the device must stay usable, and a handle with the
+    # default bound must then solve the same step
+    from paper_2204_10822_gb300 import SvnError
+    p = W.config(0, N=64)
+    s = make_solver(p, precision="mixed", cheb_fuse=5, wait_polls=1)
+    with pytest.raises(SvnError) as e:
+        s.step(p.dt, 1e-8)
+    assert e.value.status == "SVN_ERR_TIMEOUT", e.value
+    s.close()
+    s = make_solver(p, precision="mixed", cheb_fuse=5)
+    _, st = s.step(p.dt, 1e-8)
+    assert st["status"] == "SVN_OK"
 
 
 def test_krylov_solve_parity():
