@@ -59,6 +59,11 @@ def parse():
     ap.add_argument("--no-learned", action="store_true", help="skip training / using the learned initial guess")
     ap.add_argument("--learned-traj", type=int, default=64)
     ap.add_argument("--learned-epochs", type=int, default=25)
+    ap.add_argument("--vcycle-probe", type=int, default=None, metavar="CHEB_FUSE",
+                    help="profiling aid: linearise the N^2 mixed workload at a random state and apply three "
+                         "V-cycles with the given two-step sweep kernel setting")
+    ap.add_argument("--q2", action="store_true",
+                    help="Q2 velocity elements: the 2048^2-cell recipe on 1024^2 Q2 cells (same 8.4M DOF)")
     ap.add_argument("--learned-c4", action="store_true",
                     help="learned-start study: train on 2000 solver pairs at 256^2, test at 256^2 and 1024^2")
     return ap.parse_args()
@@ -525,6 +530,71 @@ def run_ensemble(args):
             "krylov_iters_mean": float(np.mean([x["krylov_iters_total"] for x in st]))}
 
 
+def run_vcycle_probe(args):
+    """Three V-cycles of the mixed path at N^2 with the chosen cheb_fuse setting:
+    the small, self-contained command that the sweep kernels' ncu captures run."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2204_10822_gb300 import Solver
+
+    N = args.N
+    p = W.make_problem(N, seed=13)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    s = Solver(N, p.L, precision="mixed", cheb_degree=6, cheb_lo=0.02, cheb_fuse=args.vcycle_probe)
+    s.set_forcing(t(p.h), t(p.A), t(p.wind), t(p.ocean), t(p.v_old))
+    rng = np.random.default_rng(13)
+    v = np.zeros((N + 1, N + 1, 2))
+    v[1:-1, 1:-1] = 0.05 * rng.standard_normal((N - 1, N - 1, 2))
+    s.linearize(p.dt, t(v), t(np.zeros(s.pi_shape)))
+    r = t(rng.standard_normal((N + 1, N + 1, 2)))
+    for _ in range(3):
+        z = s.precondition(r)
+    torch.cuda.synchronize()
+    return {"probe": "vcycle", "N": N, "cheb_fuse": args.vcycle_probe, "max_abs": float(z.abs().max())}
+
+
+def run_q2(args):
+    """Q2 velocity elements on the synthetic recipe: N x N Q2 cells carry the same
+    (2N+1)^2 nodes as the 2N x 2N Q1 workload; one implicit step, timed after
+    warm-up, for the mixed and the FP64 preconditioner."""
+    import numpy as np
+    import torch
+
+    import workloads as W
+    from paper_2204_10822_gb300 import Q2Solver
+
+    N = args.N // 2
+    p = W.make_problem_q2(N, seed=2)
+    t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    out = {}
+    for prec in ("mixed", "fp64"):
+        s = Q2Solver(N, p.L, **dict(SETTINGS, precision=prec))
+        s.set_forcing(t(p.h), t(p.A), t(p.wind), t(p.ocean), t(p.v_old))
+        for _ in range(max(1, args.warmup)):
+            s.step(p.dt, args.tol)
+        torch.cuda.synchronize()
+        times, st = [], None
+        for _ in range(args.steps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            _, st = s.step(p.dt, args.tol)
+            e1.record()
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1) / 1000.0)
+        out[prec] = {"s_per_step": statistics.mean(times), "newton_iters": st["newton_iters"],
+                     "krylov_iters": st["krylov_iters_total"], "rel_res_final": st["rel_res_final"]}
+        s.close()
+    dof = 2 * (2 * N + 1) ** 2
+    return {"metric": "s/implicit step, Q2 velocity elements (rel-res %.0e)" % args.tol,
+            "value": out["mixed"]["s_per_step"], "unit": "s/step", "higher_is_better": False, "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
+            "config": {"workload": "svN implicit step on %dx%d Q2 cells (%d DOF, the nodes of the %dx%d Q1 "
+                                   "workload), dt=1800 s, Delta_min=2e-9" % (N, N, dof, 2 * N, 2 * N)},
+            "mixed": out["mixed"], "fp64": out["fp64"]}
+
+
 def run_learned_c4(args):
     """Learned initial guess on its own workload: 200 translating-vortex trajectories
     x 10 steps at 256^2 (2000 solver-generated pairs, seeds 10000+) train the network;
@@ -667,6 +737,12 @@ def main():
         return 0
     if args.learned_c4:
         print(json.dumps(run_learned_c4(args)))
+        return 0
+    if args.q2:
+        print(json.dumps(run_q2(args)))
+        return 0
+    if args.vcycle_probe is not None:
+        print(json.dumps(run_vcycle_probe(args)))
         return 0
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))

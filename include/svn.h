@@ -292,6 +292,49 @@ int svn_residual_noalloc(const svn_grid* grid, const svn_params* prm, double dt,
                          const double* ocean, const double* v_old, const double* v,
                          double* R, double* norm, void* cuda_stream);
 
+/* ---- Q2 velocity elements (Section 5.1: the implementation "also allows
+ * higher-order discretizations"; Section 5.3 shows Problem II with quadratic
+ * velocity elements).  The same implicit step, energy, svN linearisation and
+ * dual update as above on biquadratic elements: N x N cells (N even,
+ * 4 <= N <= 8192), each with the 9 Lagrange nodes of the tensor-product
+ * quadratic basis, so the velocity lives on the (2N+1) x (2N+1) node grid of
+ * spacing dx/2 (node (I, J) at (I dx/2, J dx/2), v = 0 on the boundary); H and
+ * A constant per cell; 3 x 3 Gauss points per cell (R is the exact gradient
+ * of the discrete energy); pi at the 9 points.
+ * Layouts (device, FP64, caller-owned):
+ *   cell field   : N*N, index j*N + i (as above)
+ *   node vector  : 2*(2N+1)^2, index 2*(J*(2N+1) + I) + k
+ *   dual state pi: 27*N*N, index ((j*N + i)*9 + q)*3 + c with point
+ *                  q = 3*qb + qa at local coordinates (x[qa], x[qb]),
+ *                  x = 1/2 - sqrt(3/5)/2, 1/2, 1/2 + sqrt(3/5)/2, c as above.
+ * Linear systems: FGMRES on the FP64 Q2 Jacobian, preconditioned by the
+ * V-cycle of the Q1 operator on the same nodes (the 2N grid, linearised at
+ * the same node velocities), in the precision of params->precision.
+ * svn_q2_create allocates all workspace (including a Q1 handle on the 2N
+ * grid); on failure *out is still set (unless out is NULL) for
+ * svn_q2_last_error and must be released with svn_q2_destroy.
+ * svn_q2_set_forcing checks its inputs as svn_set_forcing does.
+ * svn_q2_step: one implicit step from v^n (damped svN, Section 4.2, with the
+ * backtracking of Section 5.1 and the retry_alpha safeguard); out_v and
+ * stats as for svn_step.  svn_q2_residual / _energy / _linearize / _apply /
+ * _dual_update: the hot-path rows on Q2 elements (svn_q2_apply multiplies by
+ * the operator of the last svn_q2_linearize).  svn_q2_get_state: the last
+ * iterate and its pi. ---- */
+typedef struct svn_q2 svn_q2;
+int svn_q2_create(const svn_grid* g, const svn_params* p, void* cuda_stream, svn_q2** out);
+int svn_q2_destroy(svn_q2* h);
+const char* svn_q2_last_error(const svn_q2* h);
+int svn_q2_set_forcing(svn_q2* h, const double* hcell, const double* A, const double* wind,
+                       const double* ocean, const double* v_old);
+int svn_q2_step(svn_q2* h, double dt, double tol, double* out_v, svn_stats* stats);
+int svn_q2_residual(svn_q2* h, double dt, const double* v, double* R, double* norm);
+int svn_q2_energy(svn_q2* h, double dt, const double* v, const double* dv, const double* alphas, int k,
+                  double* phi, double* scale);
+int svn_q2_linearize(svn_q2* h, double dt, const double* v, const double* pi);
+int svn_q2_apply(svn_q2* h, const double* x, double* y);
+int svn_q2_dual_update(svn_q2* h, double dt, const double* v, const double* dv, double alpha, double* pi);
+int svn_q2_get_state(svn_q2* h, double* v, double* pi);
+
 /* ---- Ensembles (no counterpart in the paper: the paper solves one
  * instance at a time).  n independent instances of any grid sizes; each
  * has its own handle and private non-blocking stream, and svn_batch_step

@@ -5,4 +5,4 @@ The compute path is the CUDA library ``libsvn.so`` (C ABI in
 ``include/svn.h``); this package only marshals arguments.  PyTorch provides
 device memory and streams.
 """
-from .solver import Batch, Solver, SvnError, default_params  # noqa: F401
+from .solver import Batch, Q2Solver, Solver, SvnError, default_params  # noqa: F401

@@ -93,6 +93,19 @@ _SIGS = {
     "svn_batch_step": (c_int, [c_void_p, c_double, c_double, ctypes.POINTER(c_void_p), ctypes.POINTER(SvnStats)]),
     "svn_autotune": (c_int, [c_void_p, c_double, c_int, ctypes.POINTER(c_int), c_int, P_double, c_int, P_double]),
     "svn_get_params": (c_int, [c_void_p, ctypes.POINTER(SvnParams)]),
+    "svn_q2_create": (c_int, [ctypes.POINTER(SvnGrid), ctypes.POINTER(SvnParams), c_void_p,
+                              ctypes.POINTER(c_void_p)]),
+    "svn_q2_destroy": (c_int, [c_void_p]),
+    "svn_q2_last_error": (ctypes.c_char_p, [c_void_p]),
+    "svn_q2_set_forcing": (c_int, [c_void_p] + [c_void_p] * 5),
+    "svn_q2_step": (c_int, [c_void_p, c_double, c_double, c_void_p, ctypes.POINTER(SvnStats)]),
+    "svn_q2_residual": (c_int, [c_void_p, c_double, c_void_p, c_void_p, ctypes.POINTER(c_double)]),
+    "svn_q2_energy": (c_int, [c_void_p, c_double, c_void_p, c_void_p, ctypes.POINTER(c_double), c_int,
+                              ctypes.POINTER(c_double), ctypes.POINTER(c_double)]),
+    "svn_q2_linearize": (c_int, [c_void_p, c_double, c_void_p, c_void_p]),
+    "svn_q2_apply": (c_int, [c_void_p, c_void_p, c_void_p]),
+    "svn_q2_dual_update": (c_int, [c_void_p, c_double, c_void_p, c_void_p, c_double, c_void_p]),
+    "svn_q2_get_state": (c_int, [c_void_p, c_void_p, c_void_p]),
     "svn_net_create": (c_int, [c_int, c_int, c_void_p, ctypes.POINTER(c_void_p)]),
     "svn_net_destroy": (c_int, [c_void_p]),
     "svn_net_last_error": (ctypes.c_char_p, [c_void_p]),

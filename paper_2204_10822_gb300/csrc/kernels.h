@@ -74,6 +74,8 @@ void launch_q2_element_matrices(cudaStream_t s, const Q2Geom& q, const Phys& ph,
 void launch_q2_apply(cudaStream_t s, const Q2Geom& q, const double* ke, const double2* x, double* eb, double2* y);
 void launch_q2_dual_update(cudaStream_t s, const Q2Geom& q, const Phys& ph, double alpha, const double2* v,
                            const double2* dv, double* pi);
+void launch_q2_refine_cells(cudaStream_t s, int N, const double* src, double* dst);   // N^2 -> (2N)^2 cells
+void launch_q2_pi_layout(cudaStream_t s, const Q2Geom& q, const double* src, double* dst, bool to_planes);
 
 // ---- transport of A and H (transport.cu) ----
 int transport_courant_blocks(int N);

@@ -484,6 +484,29 @@ __global__ void k_q2_dual_update(int N, Layout gq, long long cpl, Phys ph, doubl
 // Caller layout <-> padded node layout for the (2N+1)^2 Q2 nodes is the Q1
 // layout of a 2N grid (launch_unpack_nodes / launch_pack_nodes with gq).
 
+// Cell field of the N grid -> the 2N grid (each cell to its four sub-cells).
+__global__ void k_q2_refine_cells(int N, const double* __restrict__ src, double* __restrict__ dst) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= 2 * N || j >= 2 * N) return;
+  dst[(long long)j * 2 * N + i] = src[(long long)(j >> 1) * N + (i >> 1)];
+}
+
+// dual state, caller layout ((j N + i) 9 + q) 3 + c  <->  27 planes of cpl
+__global__ void k_q2_pi_layout(int N, long long cpl, const double* __restrict__ src, double* __restrict__ dst,
+                               int to_planes) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int j = blockIdx.y * blockDim.y + threadIdx.y;
+  if (i >= N || j >= N) return;
+  const long long c = (long long)j * N + i;
+  for (int t = 0; t < 27; ++t) {
+    if (to_planes)
+      dst[t * cpl + c] = src[c * 27 + t];
+    else
+      dst[c * 27 + t] = src[t * cpl + c];
+  }
+}
+
 }  // namespace
 
 // ---- host side -----------------------------------------------------------------------
@@ -566,6 +589,14 @@ void launch_q2_apply(cudaStream_t s, const Q2Geom& q, const double* ke, const do
   k_q2_apply_cells<<<q2_cell_grid(q.N), kQBlk, 0, s>>>(q.N, q.gq, q.cpl, ke, x, eb);
   note_launch();
   k_q2_gather<<<q2_node_grid(2 * q.N + 1), kQBlk, 0, s>>>(q.N, q.gq, q.cpl, eb, y, nullptr);
+}
+void launch_q2_refine_cells(cudaStream_t s, int N, const double* src, double* dst) {
+  note_launch();
+  k_q2_refine_cells<<<q2_cell_grid(2 * N), kQBlk, 0, s>>>(N, src, dst);
+}
+void launch_q2_pi_layout(cudaStream_t s, const Q2Geom& q, const double* src, double* dst, bool to_planes) {
+  note_launch();
+  k_q2_pi_layout<<<q2_cell_grid(q.N), kQBlk, 0, s>>>(q.N, q.cpl, src, dst, to_planes ? 1 : 0);
 }
 void launch_q2_dual_update(cudaStream_t s, const Q2Geom& q, const Phys& ph, double alpha, const double2* v,
                            const double2* dv, double* pi) {

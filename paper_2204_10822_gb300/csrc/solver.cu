@@ -16,6 +16,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <functional>
 #include <new>
 #include <string>
 #include <vector>
@@ -92,6 +93,10 @@ struct svn_handle {
 
   // learned initial guess (not owned)
   svn::NetImpl* net = nullptr;
+
+  // when set, the outer Krylov operator (the Q2 discretisation uses this
+  // handle's V-cycle and FGMRES workspace around its own operator)
+  std::function<void(const double2*, double2*)> outer;
 
   // the V-cycle as a CUDA graph: input in lv[0].b, output in lv[0].x[1]
   cudaGraph_t vc_graph = nullptr;
@@ -542,7 +547,10 @@ int precondition(svn_handle* h, const double2* r, double2* z) {
 // y = K0 z (FP64 outer operator).
 void apply_outer(svn_handle* h, const double2* z, double2* y) {
   Prof pr(h, SVN_K_APPLY);
-  launch_apply<double, double2, double2, double>(h->stream, h->g0, h->lv[0].st64, z, y);
+  if (h->outer)
+    h->outer(z, y);
+  else
+    launch_apply<double, double2, double2, double>(h->stream, h->g0, h->lv[0].st64, z, y);
 }
 
 double2* zvec(svn_handle* h, int j) { return h->Z + (size_t)j * h->g0.plane; }
@@ -657,7 +665,7 @@ int fgmres(svn_handle* h, const double2* b, double2* x, double rtol, int maxit, 
     if (est <= rtol * bnorm) break;
     if (total >= maxit) break;   // inexact Newton direction; the line search safeguards it
     // restart: V0 = (b - K x) / |b - K x|
-    launch_apply<double, double2, double2, double>(s, g, h->lv[0].st64, x, h->w);
+    apply_outer(h, x, h->w);
     launch_axpby_to(s, g, b, -1.0, h->w, h->w);
     CKL();
     TRY(norm2(h, h->w, &beta));
@@ -1090,6 +1098,282 @@ int step_impl(svn_handle* h, double dt, double tol, svn_stats* st) {
     CKL();
     phi0 = phi1;
     scale0 = scale1;
+  }
+  CK(cudaStreamSynchronize(s));
+  st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+  return SVN_OK;
+}
+
+// ---- Q2 velocity elements ----------------------------------------------------------
+// The Q2 step owns its cell and quadrature data and borrows a Q1 handle on the
+// 2N grid (the same (2N+1)^2 nodes): its FGMRES workspace, and its V-cycle of
+// the Q1 operator linearised at the same node velocities (with the Q1 points'
+// own pi = tau/Delta) as the preconditioner -- Q1 on the refined grid is
+// spectrally equivalent to Q2 on the coarse one, and FGMRES only needs an
+// approximate inverse.  The outer operator is the FP64 Q2 Jacobian.
+}  // namespace
+
+struct svn_q2 {
+  svn_grid grid{};
+  svn_params prm{};
+  svn_handle* pre = nullptr;         // Q1 handle on the 2N grid (owned)
+  std::string err;
+  Q2Geom q{};
+  double *in_h = nullptr, *in_A = nullptr, *in_wind = nullptr, *in_ocean = nullptr, *in_vold = nullptr;
+  double *h2 = nullptr, *A2 = nullptr;   // cell fields refined to the 2N grid
+  double *P = nullptr, *rhoH = nullptr, *fq = nullptr, *voq = nullptr, *pi = nullptr, *ke = nullptr, *eb = nullptr;
+  double *pi_scratch = nullptr;
+  double2 *v = nullptr, *dv = nullptr, *vt = nullptr, *R = nullptr, *rhs = nullptr;
+  double *partial = nullptr, *scal = nullptr;
+  bool have_forcing = false;
+  double cur_dt = -1.0;
+};
+
+namespace {
+
+Phys q2_phys(const svn_q2* Q, double dt) {
+  Phys ph = make_phys(Q->pre, Q->pre->g0, dt);
+  ph.dx = Q->grid.L / Q->grid.N;      // Q2 cell width (the Q1 grid has half of it)
+  ph.idx = 1.0 / ph.dx;
+  ph.w = ph.dx * ph.dx;
+  return ph;
+}
+
+int q2_create_impl(svn_q2* Q, const svn_grid* g, const svn_params* p, void* stream) {
+  svn_grid g2{2 * g->N, g->L};
+  if (g->N < 4 || g->N > 8192 || (g->N & 1)) {
+    Q->err = "Q2: N must be even and in [4, 8192]";
+    return SVN_ERR_ARG;
+  }
+  svn_params pp = *p;
+  pp.fused_trial = 0;
+  pp.learned = 0;
+  const int rc = svn_create(&g2, &pp, stream, &Q->pre);
+  if (rc != SVN_OK) {
+    Q->err = Q->pre ? Q->pre->err : std::string("Q2: preconditioner handle");
+    return rc;
+  }
+  svn_handle* h = Q->pre;
+  Q->grid = *g;
+  Q->prm = *p;
+  if (q2_init_tables() != 0) return fail(h, SVN_ERR_CUDA, "Q2 basis tables");
+  Q->q.N = g->N;
+  Q->q.cpl = ((long long)g->N * g->N + 63) / 64 * 64;
+  Q->q.gq = h->g0;
+  const long long cpl = Q->q.cpl, pl = h->g0.plane;
+  const size_t nc = (size_t)g->N * g->N, nv = 2 * (size_t)(2 * g->N + 1) * (2 * g->N + 1);
+  TRY(dalloc(h, &Q->in_h, nc));
+  TRY(dalloc(h, &Q->in_A, nc));
+  TRY(dalloc(h, &Q->in_wind, nv));
+  TRY(dalloc(h, &Q->in_ocean, nv));
+  TRY(dalloc(h, &Q->in_vold, nv));
+  TRY(dalloc(h, &Q->h2, 4 * nc));
+  TRY(dalloc(h, &Q->A2, 4 * nc));
+  TRY(dalloc(h, &Q->P, cpl));
+  TRY(dalloc(h, &Q->rhoH, cpl));
+  TRY(dalloc(h, &Q->fq, 18 * cpl));
+  TRY(dalloc(h, &Q->voq, 18 * cpl));
+  TRY(dalloc(h, &Q->pi, 27 * cpl));
+  TRY(dalloc(h, &Q->pi_scratch, 27 * cpl));
+  TRY(dalloc(h, &Q->ke, 171 * cpl));
+  TRY(dalloc(h, &Q->eb, 18 * cpl));
+  TRY(dalloc(h, &Q->v, pl));
+  TRY(dalloc(h, &Q->dv, pl));
+  TRY(dalloc(h, &Q->vt, pl));
+  TRY(dalloc(h, &Q->R, pl));
+  TRY(dalloc(h, &Q->rhs, pl));
+  const size_t np = std::max<size_t>({(size_t)q2_node_partials(Q->q),
+                                      (size_t)q2_energy_partials(Q->q) * (2 * MAX_ALPHA + 1), 4096});
+  TRY(dalloc(h, &Q->partial, np));
+  TRY(dalloc(h, &Q->scal, 64));
+  return SVN_OK;
+}
+
+void q2_destroy_impl(svn_q2* Q) {
+  dfree(Q->in_h); dfree(Q->in_A); dfree(Q->in_wind); dfree(Q->in_ocean); dfree(Q->in_vold);
+  dfree(Q->h2); dfree(Q->A2); dfree(Q->P); dfree(Q->rhoH); dfree(Q->fq); dfree(Q->voq); dfree(Q->pi);
+  dfree(Q->pi_scratch); dfree(Q->ke); dfree(Q->eb);
+  dfree(Q->v); dfree(Q->dv); dfree(Q->vt); dfree(Q->R); dfree(Q->rhs); dfree(Q->partial); dfree(Q->scal);
+  if (Q->pre) svn_destroy(Q->pre);
+  Q->pre = nullptr;
+}
+
+int q2_precompute(svn_q2* Q, double dt) {
+  svn_handle* h = Q->pre;
+  if (!Q->have_forcing) return fail(h, SVN_ERR_STATE, "svn_q2_set_forcing has not been called");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(h, SVN_ERR_ARG, "dt must be positive and finite");
+  launch_q2_precompute(h->stream, Q->q, dt, make_pc(Q->prm), Q->in_h, Q->in_A, Q->in_wind, Q->in_ocean, Q->in_vold,
+                       Q->P, Q->rhoH, Q->fq, Q->voq);
+  CKL();
+  TRY(precompute(h, dt));    // the preconditioner's fields on the 2N grid
+  Q->cur_dt = dt;
+  return SVN_OK;
+}
+
+int q2_residual(svn_q2* Q, const double2* v, double2* R, double* norm) {
+  svn_handle* h = Q->pre;
+  {
+    Prof pr(h, SVN_K_RESIDUAL);
+    launch_q2_residual(h->stream, Q->q, q2_phys(Q, Q->cur_dt), v, Q->P, Q->rhoH, Q->fq, Q->voq, Q->eb, R,
+                       Q->partial);
+  }
+  launch_sum_final(h->stream, Q->partial, q2_node_partials(Q->q), Q->scal);
+  CKL();
+  double s2;
+  TRY(sync_read(h, Q->scal, 1, &s2));
+  *norm = std::sqrt(s2);
+  return SVN_OK;
+}
+
+int q2_energy(svn_q2* Q, const double2* v, const double2* dv, const double* alphas, int k, double* phi,
+              double* scale) {
+  svn_handle* h = Q->pre;
+  if (k < 1 || k > MAX_ALPHA) return fail(h, SVN_ERR_ARG, "energy: 1 <= k <= %d", MAX_ALPHA);
+  AlphaSet al{};
+  for (int a = 0; a < k; ++a) al.a[a] = alphas[a];
+  {
+    Prof pr(h, SVN_K_ENERGY);
+    launch_q2_energy(h->stream, Q->q, q2_phys(Q, Q->cur_dt), k, al, v, dv, Q->P, Q->rhoH, Q->fq, Q->voq, Q->partial,
+                     Q->scal);
+  }
+  CKL();
+  double out[MAX_ALPHA + 1];
+  TRY(sync_read(h, Q->scal, MAX_ALPHA + 1, out));
+  for (int a = 0; a < k; ++a) phi[a] = out[a];
+  if (scale) *scale = out[MAX_ALPHA];
+  return SVN_OK;
+}
+
+// Q2 element matrices at (v, pi) and the preconditioner's Q1 hierarchy at v.
+int q2_linearize(svn_q2* Q, const double2* v, const double* pi) {
+  svn_handle* h = Q->pre;
+  {
+    Prof pr(h, SVN_K_ELEMENT);
+    launch_q2_element_matrices(h->stream, Q->q, q2_phys(Q, Q->cur_dt), v, pi, Q->P, Q->rhoH, Q->voq, Q->ke);
+  }
+  CKL();
+  launch_pi_init(h->stream, h->g0, make_phys(h, h->g0, h->cur_dt), v, h->pi);
+  CKL();
+  TRY(linearize(h, v, h->pi));
+  Q->pre->outer = [Q](const double2* x, double2* y) {
+    launch_q2_apply(Q->pre->stream, Q->q, Q->ke, x, Q->eb, y);
+  };
+  return SVN_OK;
+}
+
+// One implicit step on Q2 elements: the damped svN iteration of step_impl with
+// the Q2 residual, energy, operator and dual update (Sections 4.2 and 5.1).
+int q2_step_impl(svn_q2* Q, double dt, double tol, svn_stats* st) {
+  svn_handle* h = Q->pre;
+  auto t0 = std::chrono::steady_clock::now();
+  cudaStream_t s = h->stream;
+  const Layout& g = Q->q.gq;
+  st->status = SVN_OK;
+  TRY(q2_precompute(Q, dt));
+  if (!(tol > 0.0)) return fail(h, SVN_ERR_ARG, "tol must be positive");
+  const Phys ph = q2_phys(Q, dt);
+  launch_unpack_nodes(s, g, Q->in_vold, Q->v);
+  CKL();
+  TRY(q2_residual(Q, Q->v, Q->R, &st->res0));
+  launch_q2_pi_init(s, Q->q, ph, Q->v, Q->pi);
+  CKL();
+  const svn_params& p = Q->prm;
+  double phi0, scale0;
+  {
+    const double a0 = 0.0;
+    TRY(q2_energy(Q, Q->v, Q->v, &a0, 1, &phi0, &scale0));
+  }
+  double eta_prev = p.ew_eta_max;
+  for (int it = 0;; ++it) {
+    double r;
+    TRY(q2_residual(Q, Q->v, Q->R, &r));
+    st->res_hist[it] = r;
+    st->newton_iters = it;
+    st->res_final = r;
+    st->rel_res_final = st->res0 > 0 ? r / st->res0 : 0.0;
+    if (!std::isfinite(r)) return fail(h, SVN_ERR_NONFINITE, "non-finite residual norm at Newton iteration %d", it);
+    if (r <= tol * st->res0 || r == 0.0) break;
+    if (it >= p.max_newton)
+      return fail(h, SVN_ERR_NO_CONVERGENCE, "no convergence in %d Newton iterations (rel-res %.3e)", it,
+                  st->rel_res_final);
+    if (p.method == 1) {
+      launch_q2_pi_init(s, Q->q, ph, Q->v, Q->pi);
+      CKL();
+    }
+    TRY(q2_linearize(Q, Q->v, Q->pi));
+    launch_neg_copy(s, g, Q->R, Q->rhs);
+    CKL();
+    double eta = p.krylov_rtol;
+    if (p.eisenstat_walker) {
+      eta = p.ew_eta_max;
+      if (it > 0) {
+        const double ratio = r / st->res_hist[it - 1];
+        eta = 0.9 * ratio * ratio;
+        const double prev = 0.9 * eta_prev * eta_prev;
+        if (prev > 0.1) eta = std::max(eta, prev);
+        eta = std::min(p.ew_eta_max, std::max(p.krylov_rtol, eta));
+      }
+      eta_prev = eta;
+    }
+    // FGMRES on the Q2 operator, backtracking on Phi in batches of eight step
+    // lengths per energy pass, and the retry_alpha safeguard of step_impl
+    double alpha = 1.0, phi1 = 0.0, scale1 = 0.0;
+    bool ok = false;
+    for (int attempt = 0;; ++attempt) {
+      int kits = 0;
+      TRY(fgmres(h, Q->rhs, Q->dv, eta, p.max_krylov, &kits));
+      st->krylov_per_newton[it] += kits;
+      st->krylov_iters_total += kits;
+      ok = false;
+      double a = 1.0;
+      for (int k0 = 0; k0 <= p.max_halvings && !ok; k0 += MAX_ALPHA) {
+        const int nk = std::min(MAX_ALPHA, p.max_halvings + 1 - k0);
+        double al[MAX_ALPHA], ph_[MAX_ALPHA];
+        for (int k = 0; k < nk; ++k) al[k] = a * std::ldexp(1.0, -k);
+        TRY(q2_energy(Q, Q->v, Q->dv, al, nk, ph_, &scale1));
+        for (int k = 0; k < nk && !ok; ++k) {
+          if (ph_[k] < phi0) {
+            ok = true;
+          } else if (std::fabs(ph_[k] - phi0) <= p.ls_floor * scale0) {
+            launch_axpby_to(s, g, Q->v, al[k], Q->dv, Q->vt);
+            CKL();
+            double rn;
+            TRY(q2_residual(Q, Q->vt, h->w, &rn));   // h->w: Krylov scratch, free after FGMRES
+            ok = rn < r;
+          }
+          if (ok) {
+            alpha = al[k];
+            phi1 = ph_[k];
+            st->halvings_total += k0 + k;
+          }
+        }
+        a = std::ldexp(a, -nk);
+      }
+      if (!ok) st->halvings_total += p.max_halvings;
+      const bool short_step = !ok || alpha < p.retry_alpha;
+      if (short_step && eta > p.krylov_rtol && attempt < 3) {
+        eta = std::max(p.krylov_rtol, 0.01 * eta);
+        eta_prev = eta;
+        st->direction_retries += 1;
+        continue;
+      }
+      break;
+    }
+    if (!ok) return fail(h, SVN_ERR_LINESEARCH, "line search failed after %d halvings", p.max_halvings);
+    st->alpha_hist[it] = alpha;
+    if (p.method == 0) {
+      Prof pr(h, SVN_K_DUAL);
+      launch_q2_dual_update(s, Q->q, ph, alpha, Q->v, Q->dv, Q->pi);
+    }
+    launch_axpy(s, g, alpha, Q->dv, Q->v);
+    CKL();
+    phi0 = phi1;
+    // the rounding scale of Phi at the new iterate (one more energy pass)
+    {
+      const double a0 = 0.0;
+      double dummy;
+      TRY(q2_energy(Q, Q->v, Q->v, &a0, 1, &dummy, &scale0));
+    }
   }
   CK(cudaStreamSynchronize(s));
   st->seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1534,6 +1818,146 @@ int svn_autotune(svn_handle* h, double dt, int probe_newton, const int* degrees,
   h->prm.cheb_lo = bl;
   h->graph_dirty = true;
   if (best_ms) *best_ms = best;
+  return SVN_OK;
+}
+
+// ---- Q2 velocity elements ------------------------------------------------------------
+int svn_q2_create(const svn_grid* g, const svn_params* p, void* cuda_stream, svn_q2** out) {
+  if (!out) return SVN_ERR_ARG;
+  *out = nullptr;
+  if (!g || !p) return SVN_ERR_ARG;
+  svn_q2* Q = new (std::nothrow) svn_q2();
+  if (!Q) return SVN_ERR_OOM;
+  const int rc = q2_create_impl(Q, g, p, cuda_stream);
+  if (rc != SVN_OK) {
+    if (Q->pre && !Q->pre->err.empty()) Q->err = Q->pre->err;
+    q2_destroy_impl(Q);
+  }
+  *out = Q;
+  return rc;
+}
+
+int svn_q2_destroy(svn_q2* Q) {
+  if (!Q) return SVN_ERR_ARG;
+  q2_destroy_impl(Q);
+  delete Q;
+  return SVN_OK;
+}
+
+const char* svn_q2_last_error(const svn_q2* Q) {
+  if (!Q) return "NULL handle";
+  return (Q->pre && !Q->pre->err.empty()) ? Q->pre->err.c_str() : Q->err.c_str();
+}
+
+int svn_q2_set_forcing(svn_q2* Q, const double* hc, const double* A, const double* wind, const double* ocean,
+                       const double* v_old) {
+  if (!Q || !Q->pre) return SVN_ERR_ARG;
+  svn_handle* h = Q->pre;
+  if (!hc || !A || !wind || !ocean || !v_old) return fail(h, SVN_ERR_ARG, "NULL forcing pointer");
+  const int N = Q->grid.N;
+  const size_t nc = (size_t)N * N, nv = 2 * (size_t)(2 * N + 1) * (2 * N + 1);
+  cudaStream_t s = h->stream;
+  CK(cudaMemcpyAsync(Q->in_h, hc, sizeof(double) * nc, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(Q->in_A, A, sizeof(double) * nc, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(Q->in_wind, wind, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(Q->in_ocean, ocean, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
+  CK(cudaMemcpyAsync(Q->in_vold, v_old, sizeof(double) * nv, cudaMemcpyDeviceToDevice, s));
+  launch_q2_refine_cells(s, N, Q->in_h, Q->h2);
+  launch_q2_refine_cells(s, N, Q->in_A, Q->A2);
+  CKL();
+  Q->have_forcing = false;
+  // the preconditioner's copy (and the checks of svn_set_forcing)
+  TRY(set_forcing_impl(h, Q->h2, Q->A2, Q->in_wind, Q->in_ocean, Q->in_vold, false));
+  Q->have_forcing = true;
+  return SVN_OK;
+}
+
+int svn_q2_step(svn_q2* Q, double dt, double tol, double* out_v, svn_stats* stats) {
+  if (!Q || !Q->pre) return SVN_ERR_ARG;
+  svn_handle* h = Q->pre;
+  svn_stats local;
+  svn_stats* st = stats ? stats : &local;
+  memset(st, 0, sizeof(*st));
+  int rc = q2_step_impl(Q, dt, tol, st);
+  st->status = rc;
+  if (out_v) {
+    launch_pack_nodes(h->stream, Q->q.gq, Q->v, out_v);
+    const cudaError_t e = cudaStreamSynchronize(h->stream);
+    if (e != cudaSuccess && rc == SVN_OK) rc = fail(h, SVN_ERR_CUDA, "output copy: %s", cudaGetErrorString(e));
+  }
+  return rc;
+}
+
+int svn_q2_residual(svn_q2* Q, double dt, const double* v, double* R, double* norm) {
+  if (!Q || !Q->pre || !v || !R) return SVN_ERR_ARG;
+  svn_handle* h = Q->pre;
+  TRY(q2_precompute(Q, dt));
+  launch_unpack_nodes(h->stream, Q->q.gq, v, Q->vt);
+  CKL();
+  double nrm;
+  TRY(q2_residual(Q, Q->vt, h->w, &nrm));
+  launch_pack_nodes(h->stream, Q->q.gq, h->w, R);
+  CKL();
+  CK(cudaStreamSynchronize(h->stream));
+  if (norm) *norm = nrm;
+  return SVN_OK;
+}
+
+int svn_q2_energy(svn_q2* Q, double dt, const double* v, const double* dv, const double* alphas, int k, double* phi,
+                  double* scale) {
+  if (!Q || !Q->pre || !v || !dv || !alphas || !phi) return SVN_ERR_ARG;
+  svn_handle* h = Q->pre;
+  TRY(q2_precompute(Q, dt));
+  launch_unpack_nodes(h->stream, Q->q.gq, v, Q->vt);
+  launch_unpack_nodes(h->stream, Q->q.gq, dv, Q->rhs);
+  CKL();
+  return q2_energy(Q, Q->vt, Q->rhs, alphas, k, phi, scale);
+}
+
+int svn_q2_linearize(svn_q2* Q, double dt, const double* v, const double* pi) {
+  if (!Q || !Q->pre || !v || !pi) return SVN_ERR_ARG;
+  svn_handle* h = Q->pre;
+  TRY(q2_precompute(Q, dt));
+  launch_unpack_nodes(h->stream, Q->q.gq, v, Q->vt);
+  launch_q2_pi_layout(h->stream, Q->q, pi, Q->pi_scratch, true);
+  CKL();
+  TRY(q2_linearize(Q, Q->vt, Q->pi_scratch));
+  CK(cudaStreamSynchronize(h->stream));
+  return SVN_OK;
+}
+
+int svn_q2_apply(svn_q2* Q, const double* x, double* y) {
+  if (!Q || !Q->pre || !x || !y) return SVN_ERR_ARG;
+  svn_handle* h = Q->pre;
+  launch_unpack_nodes(h->stream, Q->q.gq, x, Q->vt);
+  launch_q2_apply(h->stream, Q->q, Q->ke, Q->vt, Q->eb, h->w);
+  launch_pack_nodes(h->stream, Q->q.gq, h->w, y);
+  CKL();
+  CK(cudaStreamSynchronize(h->stream));
+  return SVN_OK;
+}
+
+int svn_q2_dual_update(svn_q2* Q, double dt, const double* v, const double* dv, double alpha, double* pi) {
+  if (!Q || !Q->pre || !v || !dv || !pi) return SVN_ERR_ARG;
+  svn_handle* h = Q->pre;
+  TRY(q2_precompute(Q, dt));
+  launch_unpack_nodes(h->stream, Q->q.gq, v, Q->vt);
+  launch_unpack_nodes(h->stream, Q->q.gq, dv, Q->rhs);
+  launch_q2_pi_layout(h->stream, Q->q, pi, Q->pi_scratch, true);
+  launch_q2_dual_update(h->stream, Q->q, q2_phys(Q, dt), alpha, Q->vt, Q->rhs, Q->pi_scratch);
+  launch_q2_pi_layout(h->stream, Q->q, Q->pi_scratch, pi, false);
+  CKL();
+  CK(cudaStreamSynchronize(h->stream));
+  return SVN_OK;
+}
+
+int svn_q2_get_state(svn_q2* Q, double* v, double* pi) {
+  if (!Q || !Q->pre || !v || !pi) return SVN_ERR_ARG;
+  svn_handle* h = Q->pre;
+  launch_pack_nodes(h->stream, Q->q.gq, Q->v, v);
+  launch_q2_pi_layout(h->stream, Q->q, Q->pi, pi, false);
+  CKL();
+  CK(cudaStreamSynchronize(h->stream));
   return SVN_OK;
 }
 

@@ -279,3 +279,98 @@ class Batch:
         if rc != 0:
             raise SvnError(rc, self.lib.svn_batch_last_error(self.b).decode())
         return outs, [s.to_dict() for s in stats]
+
+
+class Q2Solver:
+    """One svN solver on Q2 (biquadratic) velocity elements: N x N cells, node
+    vectors on the (2N+1)^2 grid, dual state (N, N, 9, 3)."""
+
+    def __init__(self, N: int, L: float = 512e3, stream=None, **params):
+        import torch
+        self.N, self.L = int(N), float(L)
+        self.lib = capi.lib()
+        self.params = default_params(**params)
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        g = capi.SvnGrid(self.N, self.L)
+        h = ctypes.c_void_p()
+        rc = self.lib.svn_q2_create(ctypes.byref(g), ctypes.byref(self.params),
+                                    ctypes.c_void_p(self.stream.cuda_stream), ctypes.byref(h))
+        self.h = h
+        if rc != 0:
+            msg = self.lib.svn_q2_last_error(h).decode() if h.value else ""
+            if h.value:
+                self.lib.svn_q2_destroy(h)
+            self.h = None
+            raise SvnError(rc, msg)
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.svn_q2_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int):
+        if rc != 0:
+            raise SvnError(rc, self.lib.svn_q2_last_error(self.h).decode())
+
+    @property
+    def node_shape(self):
+        return (2 * self.N + 1, 2 * self.N + 1, 2)
+
+    @property
+    def pi_shape(self):
+        return (self.N, self.N, 9, 3)
+
+    def _vec(self):
+        import torch
+        return torch.zeros(self.node_shape, dtype=torch.float64, device="cuda")
+
+    def set_forcing(self, h, A, wind, ocean, v_old):
+        self._check(self.lib.svn_q2_set_forcing(self.h, _ptr(h), _ptr(A), _ptr(wind), _ptr(ocean), _ptr(v_old)))
+
+    def step(self, dt: float, tol: float, out=None, raise_on_error: bool = True):
+        out = self._vec() if out is None else out
+        st = capi.SvnStats()
+        rc = self.lib.svn_q2_step(self.h, dt, tol, _ptr(out), ctypes.byref(st))
+        if rc != 0 and raise_on_error:
+            self._check(rc)
+        return out, st.to_dict()
+
+    def residual(self, dt: float, v):
+        R = self._vec()
+        nrm = ctypes.c_double()
+        self._check(self.lib.svn_q2_residual(self.h, dt, _ptr(v), _ptr(R), ctypes.byref(nrm)))
+        return R, nrm.value
+
+    def energy(self, dt: float, v, dv, alphas):
+        k = len(alphas)
+        al = (ctypes.c_double * k)(*alphas)
+        phi = (ctypes.c_double * k)()
+        scale = ctypes.c_double()
+        self._check(self.lib.svn_q2_energy(self.h, dt, _ptr(v), _ptr(dv), al, k, phi, ctypes.byref(scale)))
+        return list(phi), scale.value
+
+    def linearize(self, dt: float, v, pi):
+        self._check(self.lib.svn_q2_linearize(self.h, dt, _ptr(v), _ptr(pi)))
+
+    def apply(self, x):
+        import torch
+        y = torch.zeros_like(x)
+        self._check(self.lib.svn_q2_apply(self.h, _ptr(x), _ptr(y)))
+        return y
+
+    def dual_update(self, dt: float, v, dv, alpha: float, pi):
+        self._check(self.lib.svn_q2_dual_update(self.h, dt, _ptr(v), _ptr(dv), alpha, _ptr(pi)))
+        return pi
+
+    def get_state(self):
+        import torch
+        v = self._vec()
+        pi = torch.zeros(self.pi_shape, dtype=torch.float64, device="cuda")
+        self._check(self.lib.svn_q2_get_state(self.h, _ptr(v), _ptr(pi)))
+        return v, pi
