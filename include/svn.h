@@ -363,6 +363,18 @@ int svn_batch_step(svn_batch* b, double dt, double tol, double* const* out_v, sv
  * error the handle keeps the smoother settings it had before the call. ---- */
 int svn_autotune(svn_handle* h, double dt, int probe_newton, const int* degrees, int nd,
                  const double* los, int nl, double* best_ms);
+/* The same search over the sweep kernels too: every cheb_fuse value in
+ * cheb_fuses[nf] (each in [0, 5]: the shared-memory tile, row-streaming and
+ * TMA-staged two-step kernels and their level thresholds) times every
+ * (degree, lo) pair; the fastest triple is kept.  Callers that tune many
+ * handles of one grid size cache the result (the Python binding keeps a JSON
+ * file keyed by grid size and precision). */
+int svn_autotune_kernels(svn_handle* h, double dt, int probe_newton, const int* degrees, int nd,
+                         const double* los, int nl, const int* cheb_fuses, int nf, double* best_ms);
+/* Set the smoother settings of a handle (as svn_params.cheb_fuse,
+ * cheb_degree, cheb_lo; checked like svn_create), e.g. from a cached
+ * autotuner result; they take effect at the next linearisation. */
+int svn_set_smoother(svn_handle* h, int cheb_fuse, int cheb_degree, double cheb_lo);
 int svn_get_params(const svn_handle* h, svn_params* p);
 
 /* ---- Learned initial guess (no counterpart in the paper).  A U-Net on a

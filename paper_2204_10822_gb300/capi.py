@@ -92,6 +92,9 @@ _SIGS = {
     "svn_batch_instance": (c_void_p, [c_void_p, c_int]),
     "svn_batch_step": (c_int, [c_void_p, c_double, c_double, ctypes.POINTER(c_void_p), ctypes.POINTER(SvnStats)]),
     "svn_autotune": (c_int, [c_void_p, c_double, c_int, ctypes.POINTER(c_int), c_int, P_double, c_int, P_double]),
+    "svn_set_smoother": (c_int, [c_void_p, c_int, c_int, c_double]),
+    "svn_autotune_kernels": (c_int, [c_void_p, c_double, c_int, ctypes.POINTER(c_int), c_int, P_double, c_int,
+                                     ctypes.POINTER(c_int), c_int, P_double]),
     "svn_get_params": (c_int, [c_void_p, ctypes.POINTER(SvnParams)]),
     "svn_q2_create": (c_int, [ctypes.POINTER(SvnGrid), ctypes.POINTER(SvnParams), c_void_p,
                               ctypes.POINTER(c_void_p)]),

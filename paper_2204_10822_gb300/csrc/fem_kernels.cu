@@ -258,6 +258,7 @@ __global__ void k_energy_cells(Layout g, Phys ph, int k, AlphaSet al, const doub
       c.v10 = make_double2(c0.v10.x + al0 * d0.v10.x, c0.v10.y + al0 * d0.v10.y);
       c.v01 = make_double2(c0.v01.x + al0 * d0.v01.x, c0.v01.y + al0 * d0.v01.y);
       c.v11 = make_double2(c0.v11.x + al0 * d0.v11.x, c0.v11.y + al0 * d0.v11.y);
+      double csum = 0.0;
 #pragma unroll
       for (int q = 0; q < 4; ++q) {
         const Qp p = eval_qp(c, qxi(q), qeta(q));
@@ -273,12 +274,10 @@ __global__ void k_energy_cells(Layout g, Phys ph, int k, AlphaSet al, const doub
         const double t2 = fq[(2 * q) * g.plane + cell] * p.vx + fq[(2 * q + 1) * g.plane + cell] * p.vy;
         const double t3 = Ph * (Dl - tr);
         const double t4 = ph.dt * ph.cdrag * nw * nw * nw * (1.0 / 3.0);
-        acc[a].add(ph.w * t1);
-        acc[a].add(ph.w * t2);
-        acc[a].add(ph.w * t3);
-        acc[a].add(ph.w * t4);
+        csum += ph.w * ((t1 + t2) + (t3 + t4));
         if (a == 0) asum += ph.w * (fabs(t1) + fabs(t2) + fabs(t3) + fabs(t4));
       }
+      acc[a].add(csum);   // plain sum within the cell, compensated over cells
     }
   }
   // block reduction of the (hi, lo) pairs, then write per-block partials:
@@ -618,6 +617,9 @@ __global__ void k_trial_cells(Layout g, Phys ph, const double2* __restrict__ v, 
     const double vpw = 0.25 * ph.dx;
     const double sq2 = 1.4142135623730950488;
     double rx[4] = {0, 0, 0, 0}, ry[4] = {0, 0, 0, 0};
+    // the cell's 16 energy terms are summed in plain FP64 (their rounding is
+    // ~1e-16 of the cell's terms); the sum over cells is compensated
+    double csum = 0.0;
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const double xi = qxi(q), eta = qeta(q);
@@ -666,10 +668,7 @@ __global__ void k_trial_cells(Layout g, Phys ph, const double2* __restrict__ v, 
       const double e2 = ph.w * (fx * p.vx + fy * p.vy);
       const double e3 = ph.w * 0.5 * Pdt * (Dl - tr);
       const double e4 = ph.w * ph.dt * ph.cdrag * nw * nw * nw * (1.0 / 3.0);
-      acc.add(e1);
-      acc.add(e2);
-      acc.add(e3);
-      acc.add(e4);
+      csum += (e1 + e2) + (e3 + e4);
       asum += fabs(e1) + fabs(e2) + fabs(e3) + fabs(e4);
       const double sfac = Pdt * inv * idx;
       const double Sxx = sfac * txx, Syy = sfac * tyy, Sxy = sfac * txy;
@@ -692,6 +691,7 @@ __global__ void k_trial_cells(Layout g, Phys ph, const double2* __restrict__ v, 
         ry[k] = fma(deta, Gyy, ry[k]);
       }
     }
+    acc.add(csum);
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
       eb[(2 * k) * g.plane + cell] = rx[k];

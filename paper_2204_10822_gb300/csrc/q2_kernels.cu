@@ -276,6 +276,7 @@ __global__ void __launch_bounds__(128) k_q2_energy_cells(int N, Layout gq, long 
         L.x[n] = fma(al0, D0.x[n], L0.x[n]);
         L.y[n] = fma(al0, D0.y[n], L0.y[n]);
       }
+      double csum = 0.0;
 #pragma unroll
       for (int q = 0; q < 9; ++q) {
         const Q2Qp p = q2_eval(q, L);
@@ -291,12 +292,10 @@ __global__ void __launch_bounds__(128) k_q2_energy_cells(int N, Layout gq, long 
         const double t2 = wq * (fq[(2 * q) * cpl + c] * p.vx + fq[(2 * q + 1) * cpl + c] * p.vy);
         const double t3 = wq * Ph * (Dl - tr);
         const double t4 = wq * ph.dt * ph.cdrag * nw * nw * nw * (1.0 / 3.0);
-        acc[a].add(t1);
-        acc[a].add(t2);
-        acc[a].add(t3);
-        acc[a].add(t4);
+        csum += (t1 + t2) + (t3 + t4);
         if (a == 0) asum += fabs(t1) + fabs(t2) + fabs(t3) + fabs(t4);
       }
+      acc[a].add(csum);   // plain sum within the cell, compensated over cells
     }
   }
   __shared__ double sh_hi[128], sh_lo[128];

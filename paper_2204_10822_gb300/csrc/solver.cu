@@ -1758,13 +1758,15 @@ int svn_batch_step(svn_batch* b, double dt, double tol, double* const* out_v, sv
 // Times FGMRES on the linearisation reached after `probe_newton` Newton
 // iterations of the current forcing, for every (degree, lo) candidate, and
 // keeps the fastest in the handle's parameters.
-int svn_autotune(svn_handle* h, double dt, int probe_newton, const int* degrees, int nd, const double* los, int nl,
-                 double* best_ms) {
-  if (!h || !degrees || !los || nd < 1 || nl < 1) return SVN_ERR_ARG;
+static int autotune_impl(svn_handle* h, double dt, int probe_newton, const int* degrees, int nd, const double* los,
+                         int nl, const int* fuses, int nf, double* best_ms) {
+  if (!h || !degrees || !los || !fuses || nd < 1 || nl < 1 || nf < 1) return SVN_ERR_ARG;
   for (int i = 0; i < nd; ++i)
     if (degrees[i] < 1 || degrees[i] > 16) return fail(h, SVN_ERR_ARG, "degree out of range");
   for (int i = 0; i < nl; ++i)
     if (!(los[i] > 0.0 && los[i] < 1.0)) return fail(h, SVN_ERR_ARG, "lo out of range");
+  for (int i = 0; i < nf; ++i)
+    if (fuses[i] < 0 || fuses[i] > 5) return fail(h, SVN_ERR_ARG, "sweep kernel setting out of range");
   svn_params saved = h->prm;
   svn_stats st;
   memset(&st, 0, sizeof(st));
@@ -1776,7 +1778,7 @@ int svn_autotune(svn_handle* h, double dt, int probe_newton, const int* degrees,
   launch_neg_copy(h->stream, h->g0, h->R, h->rhs);
   CKL();
   double best = 1e300;
-  int bd = saved.cheb_degree;
+  int bd = saved.cheb_degree, bf = saved.cheb_fuse;
   double bl = saved.cheb_lo;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   // every candidate runs inside this lambda, so that an error on any of them
@@ -1784,26 +1786,29 @@ int svn_autotune(svn_handle* h, double dt, int probe_newton, const int* degrees,
   auto sweep = [&]() -> int {
     CK(cudaEventCreate(&e0));
     CK(cudaEventCreate(&e1));
-    for (int a = 0; a < nd; ++a)
-      for (int c = 0; c < nl; ++c) {
-        h->prm.cheb_degree = degrees[a];
-        h->prm.cheb_lo = los[c];
-        h->graph_dirty = true;
-        TRY(linearize(h, h->v, h->pi));
-        int its = 0;
-        TRY(fgmres(h, h->rhs, h->dv, saved.krylov_rtol, saved.max_krylov, &its));   // warm (records the graph)
-        CK(cudaEventRecord(e0, h->stream));
-        TRY(fgmres(h, h->rhs, h->dv, saved.krylov_rtol, saved.max_krylov, &its));
-        CK(cudaEventRecord(e1, h->stream));
-        CK(cudaEventSynchronize(e1));
-        float ms = 0.f;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-          best = ms;
-          bd = degrees[a];
-          bl = los[c];
+    for (int f = 0; f < nf; ++f)
+      for (int a = 0; a < nd; ++a)
+        for (int c = 0; c < nl; ++c) {
+          h->prm.cheb_degree = degrees[a];
+          h->prm.cheb_lo = los[c];
+          h->prm.cheb_fuse = fuses[f];
+          h->graph_dirty = true;
+          TRY(linearize(h, h->v, h->pi));
+          int its = 0;
+          TRY(fgmres(h, h->rhs, h->dv, saved.krylov_rtol, saved.max_krylov, &its));   // warm (records the graph)
+          CK(cudaEventRecord(e0, h->stream));
+          TRY(fgmres(h, h->rhs, h->dv, saved.krylov_rtol, saved.max_krylov, &its));
+          CK(cudaEventRecord(e1, h->stream));
+          CK(cudaEventSynchronize(e1));
+          float ms = 0.f;
+          CK(cudaEventElapsedTime(&ms, e0, e1));
+          if (ms < best) {
+            best = ms;
+            bd = degrees[a];
+            bl = los[c];
+            bf = fuses[f];
+          }
         }
-      }
     return SVN_OK;
   };
   const int rc = sweep();
@@ -1816,9 +1821,34 @@ int svn_autotune(svn_handle* h, double dt, int probe_newton, const int* degrees,
   }
   h->prm.cheb_degree = bd;
   h->prm.cheb_lo = bl;
+  h->prm.cheb_fuse = bf;
   h->graph_dirty = true;
   if (best_ms) *best_ms = best;
   return SVN_OK;
+}
+
+int svn_autotune(svn_handle* h, double dt, int probe_newton, const int* degrees, int nd, const double* los, int nl,
+                 double* best_ms) {
+  if (!h) return SVN_ERR_ARG;
+  const int fuse = h->prm.cheb_fuse;
+  return autotune_impl(h, dt, probe_newton, degrees, nd, los, nl, &fuse, 1, best_ms);
+}
+
+int svn_set_smoother(svn_handle* h, int cheb_fuse, int cheb_degree, double cheb_lo) {
+  if (!h) return SVN_ERR_ARG;
+  svn_params p = h->prm;
+  p.cheb_fuse = cheb_fuse;
+  p.cheb_degree = cheb_degree;
+  p.cheb_lo = cheb_lo;
+  TRY(check_params(h, &p));
+  h->prm = p;
+  h->graph_dirty = true;   // the V-cycle graph is recorded again; the next linearisation recomputes its coefficients
+  return SVN_OK;
+}
+
+int svn_autotune_kernels(svn_handle* h, double dt, int probe_newton, const int* degrees, int nd, const double* los,
+                         int nl, const int* cheb_fuses, int nf, double* best_ms) {
+  return autotune_impl(h, dt, probe_newton, degrees, nd, los, nl, cheb_fuses, nf, best_ms);
 }
 
 // ---- Q2 velocity elements ------------------------------------------------------------

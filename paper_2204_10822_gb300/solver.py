@@ -208,6 +208,44 @@ class Solver:
         self.params = p
         return {"cheb_degree": p.cheb_degree, "cheb_lo": p.cheb_lo, "ms": best.value}
 
+    def autotune_kernels(self, dt: float, probe_newton: int = 4, degrees=(4, 6), los=(0.02,), fuses=(1, 2, 4),
+                         cache: str | None = None):
+        """Pick the fastest (sweep kernel, Chebyshev degree, lo) for this grid and
+        forcing.  With `cache` (a JSON file path), a result stored for this grid
+        size and precision is applied without timing; a new one is stored."""
+        import json
+        import os
+        key = "%d/%d" % (self.N, self.params.precision)
+        if cache and os.path.exists(cache):
+            with open(cache) as f:
+                stored = json.load(f).get(key)
+            if stored:
+                self._check(self.lib.svn_set_smoother(self.h, stored["cheb_fuse"], stored["cheb_degree"],
+                                                      stored["cheb_lo"]))
+                p = capi.SvnParams()
+                self._check(self.lib.svn_get_params(self.h, ctypes.byref(p)))
+                self.params = p
+                return dict(stored, cached=True)
+        d = (ctypes.c_int * len(degrees))(*degrees)
+        l = (ctypes.c_double * len(los))(*los)
+        fz = (ctypes.c_int * len(fuses))(*fuses)
+        best = ctypes.c_double()
+        self._check(self.lib.svn_autotune_kernels(self.h, dt, probe_newton, d, len(degrees), l, len(los), fz,
+                                                  len(fuses), ctypes.byref(best)))
+        p = capi.SvnParams()
+        self._check(self.lib.svn_get_params(self.h, ctypes.byref(p)))
+        self.params = p
+        res = {"cheb_fuse": p.cheb_fuse, "cheb_degree": p.cheb_degree, "cheb_lo": p.cheb_lo, "ms": best.value}
+        if cache:
+            data = {}
+            if os.path.exists(cache):
+                with open(cache) as f:
+                    data = json.load(f)
+            data[key] = res
+            with open(cache, "w") as f:
+                json.dump(data, f, indent=1)
+        return dict(res, cached=False)
+
     # -- instrumentation -------------------------------------------------------
     def profile(self, enable: bool):
         self._check(self.lib.svn_profile(self.h, 1 if enable else 0))

@@ -49,3 +49,25 @@ def test_autotune_picks_a_candidate_and_still_solves():
     ref = newton(p, tol=1e-10)
     v, st = s.step(p.dt, 1e-10)
     assert np.linalg.norm(v.cpu().numpy() - ref.v) <= 1e-6 * np.linalg.norm(ref.v)
+
+
+def test_autotune_over_sweep_kernels_with_cache(tmp_path):
+    # the kernel-level autotuner chooses among the tile, row-streaming and
+    # TMA-staged sweeps, stores its choice, and a second handle of the same
+    # grid takes the stored choice without timing; both still solve the step
+    from paper_2204_10822_gb300 import Solver
+    p = W.config(0, N=64)
+    cache = str(tmp_path / "tune.json")
+    ref = newton(p, tol=1e-10)
+    results = []
+    for _ in range(2):
+        s = Solver(p.N, p.L, precision="mixed")
+        s.set_forcing(dev(p.h), dev(p.A), dev(p.wind), dev(p.ocean), dev(p.v_old))
+        best = s.autotune_kernels(p.dt, probe_newton=3, degrees=(3, 4), los=(0.05,), fuses=(2, 3, 5), cache=cache)
+        results.append(best)
+        assert best["cheb_fuse"] in (2, 3, 5) and best["cheb_degree"] in (3, 4)
+        v, st = s.step(p.dt, 1e-10)
+        assert np.linalg.norm(v.cpu().numpy() - ref.v) <= 1e-6 * np.linalg.norm(ref.v)
+        s.close()
+    assert results[0]["cached"] is False and results[1]["cached"] is True
+    assert results[1]["cheb_fuse"] == results[0]["cheb_fuse"]
