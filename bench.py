@@ -51,6 +51,7 @@ def parse():
     ap.add_argument("--ensemble", action="store_true",
                     help="ensemble workload: 64 instances, N ~ U{128,256,512,1024}, one step each")
     ap.add_argument("--ensemble-size", type=int, default=64)
+    ap.add_argument("--ensemble-threads", type=int, default=16, help="host threads driving the ensemble")
     ap.add_argument("--problem2", action="store_true",
                     help="the paper's Problem II: transport + momentum time stepping, mean Newton iterations")
     ap.add_argument("--sim-steps", type=int, default=384, help="Problem II time steps (384 x 0.5 h = 8 days)")
@@ -493,7 +494,7 @@ def run_ensemble(args):
     probs = [W.make_problem(N, seed=1000 + i) for i, N in enumerate(Ns)]
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
     kw = dict(SETTINGS, precision="mixed", vcycle_fp32=1)
-    b = Batch(Ns, host_threads=16, **kw)
+    b = Batch(Ns, host_threads=args.ensemble_threads, **kw)
     for i, p in enumerate(probs):
         b.set_forcing(i, t(p.h), t(p.A), t(p.wind), t(p.ocean), t(p.v_old))
     outs = [torch.zeros((N + 1, N + 1, 2), dtype=torch.float64, device="cuda") for N in Ns]
@@ -524,6 +525,7 @@ def run_ensemble(args):
             "dtype": "f64+f32", "data": "synthetic",
             "config": {"workload": "ensemble of %d instances, N counts %s" % (
                 len(Ns), {n: Ns.count(n) for n in (128, 256, 512, 1024)}), "dof_total": dof,
+                "host_threads": args.ensemble_threads,
                 "l2": "inputs larger than L2"},
             "sequential_s": t_seq, "batch_s": t_batch, "speedup_vs_sequential": t_seq / t_batch,
             "newton_iters_mean": float(np.mean([x["newton_iters"] for x in st])),
@@ -570,7 +572,7 @@ def run_q2(args):
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
     out = {}
     for prec in ("mixed", "fp64"):
-        s = Q2Solver(N, p.L, **dict(SETTINGS, precision=prec))
+        s = Q2Solver(N, p.L, **dict(SETTINGS, precision=prec, restart=100, max_krylov=1000))
         s.set_forcing(t(p.h), t(p.A), t(p.wind), t(p.ocean), t(p.v_old))
         for _ in range(max(1, args.warmup)):
             s.step(p.dt, args.tol)

@@ -136,6 +136,10 @@ typedef struct svn_params {
                                out abandons its block's work; the step then fails with
                                SVN_ERR_TIMEOUT (checked after each linearisation and
                                each Krylov solve; the counter is device-wide) */
+  int q2_smooth_degree;     /* Q2 elements only: Chebyshev-block-Jacobi steps on the Q2
+                               operator before and after the Q1 V-cycle of the
+                               preconditioner (p-multigrid; default 2, 0: the Q1 V-cycle
+                               alone) */
 } svn_params;
 
 typedef struct svn_stats {

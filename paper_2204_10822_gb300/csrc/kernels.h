@@ -76,6 +76,14 @@ void launch_q2_dual_update(cudaStream_t s, const Q2Geom& q, const Phys& ph, doub
                            const double2* dv, double* pi);
 void launch_q2_refine_cells(cudaStream_t s, int N, const double* src, double* dst);   // N^2 -> (2N)^2 cells
 void launch_q2_pi_layout(cudaStream_t s, const Q2Geom& q, const double* src, double* dst, bool to_planes);
+// Q2 block-Jacobi inverse (3 planes of gq.plane) from the element matrices
+void launch_q2_dinv(cudaStream_t s, const Q2Geom& q, const double* ke, double* dinv);
+// Chebyshev step k on the Q2 operator: d = c1 d + c2 D^-1 (b - Ax), x += d
+void launch_q2_cheb_step(cudaStream_t s, const Q2Geom& q, const double* dinv, const double* coef, int k,
+                         const double2* b, const double2* Ax, double2* x, double2* d);
+void launch_q2_dinv_apply(cudaStream_t s, const Q2Geom& q, const double* dinv, const double2* x, double2* y);
+// pi of the Q1 operator on the 2N grid (12 planes of gq.plane) from the Q2 pi
+void launch_q2_pi_to_q1(cudaStream_t s, const Q2Geom& q, const double* pi2, double* pi1);
 
 // ---- transport of A and H (transport.cu) ----
 int transport_courant_blocks(int N);

@@ -39,6 +39,20 @@ template <> __device__ __forceinline__ double2 mk2<double2, float>(float a, floa
 
 __device__ __forceinline__ bool is_interior(int i, int j, int N) { return i >= 1 && j >= 1 && i <= N - 1 && j <= N - 1; }
 
+// y += a xa + b xb.  FP64 stencil rows are bound by the FP64 pipe, so they
+// take two dependent FMAs (2 issues); FP32 rows are bound by memory latency,
+// so they keep the pair product independent of y (MUL + FMA, then one ADD),
+// which shortens the chain through the accumulator.
+template <typename TA>
+__device__ __forceinline__ void acc2(TA& y, TA a, TA xa, TA b, TA xb) {
+  if constexpr (std::is_same<TA, double>::value) {
+    y = fma(a, xa, y);
+    y = fma(b, xb, y);
+  } else {
+    y += a * xa + b * xb;
+  }
+}
+
 // y_p = sum_q K[p][q] x_q over the 9-point block stencil at node n.
 template <typename TA, typename TS, typename TX>
 __device__ __forceinline__ void stencil_row(const TS* __restrict__ st, long long pl, long long n, int ld,
@@ -53,19 +67,15 @@ __device__ __forceinline__ void stencil_row(const TS* __restrict__ st, long long
     const TX xq = x[q];
     const TA b0 = ldc<TA>(st + (slot + 0) * pl + n), b1 = ldc<TA>(st + (slot + 1) * pl + n);
     const TA b2 = ldc<TA>(st + (slot + 2) * pl + n), b3 = ldc<TA>(st + (slot + 3) * pl + n);
-    yx = fma(b0, (TA)xq.x, yx);
-    yx = fma(b1, (TA)xq.y, yx);
-    yy = fma(b2, (TA)xq.x, yy);
-    yy = fma(b3, (TA)xq.y, yy);
+    acc2<TA>(yx, b0, (TA)xq.x, b1, (TA)xq.y);
+    acc2<TA>(yy, b2, (TA)xq.x, b3, (TA)xq.y);
   };
   auto bwd = [&](int slot, long long q) {   // block stored at q, used transposed
     const TX xq = x[q];
     const TA b0 = ldc<TA>(st + (slot + 0) * pl + q), b1 = ldc<TA>(st + (slot + 1) * pl + q);
     const TA b2 = ldc<TA>(st + (slot + 2) * pl + q), b3 = ldc<TA>(st + (slot + 3) * pl + q);
-    yx = fma(b0, (TA)xq.x, yx);
-    yx = fma(b2, (TA)xq.y, yx);
-    yy = fma(b1, (TA)xq.x, yy);
-    yy = fma(b3, (TA)xq.y, yy);
+    acc2<TA>(yx, b0, (TA)xq.x, b2, (TA)xq.y);
+    acc2<TA>(yy, b1, (TA)xq.x, b3, (TA)xq.y);
   };
   fwd(S_E, n + 1);
   fwd(S_N, n + ld);
@@ -91,20 +101,16 @@ __device__ __forceinline__ void stencil_row_f(const TS* __restrict__ st, long lo
     const auto xq = xf(di, dj);
     const TA b0 = ldc<TA>(st + (slot + 0) * pl + n), b1 = ldc<TA>(st + (slot + 1) * pl + n);
     const TA b2 = ldc<TA>(st + (slot + 2) * pl + n), b3 = ldc<TA>(st + (slot + 3) * pl + n);
-    yx = fma(b0, (TA)xq.x, yx);
-    yx = fma(b1, (TA)xq.y, yx);
-    yy = fma(b2, (TA)xq.x, yy);
-    yy = fma(b3, (TA)xq.y, yy);
+    acc2<TA>(yx, b0, (TA)xq.x, b1, (TA)xq.y);
+    acc2<TA>(yy, b2, (TA)xq.x, b3, (TA)xq.y);
   };
   auto bwd = [&](int slot, int di, int dj) {
     const auto xq = xf(di, dj);
     const long long q = n + (long long)dj * ld + di;
     const TA b0 = ldc<TA>(st + (slot + 0) * pl + q), b1 = ldc<TA>(st + (slot + 1) * pl + q);
     const TA b2 = ldc<TA>(st + (slot + 2) * pl + q), b3 = ldc<TA>(st + (slot + 3) * pl + q);
-    yx = fma(b0, (TA)xq.x, yx);
-    yx = fma(b2, (TA)xq.y, yx);
-    yy = fma(b1, (TA)xq.x, yy);
-    yy = fma(b3, (TA)xq.y, yy);
+    acc2<TA>(yx, b0, (TA)xq.x, b2, (TA)xq.y);
+    acc2<TA>(yy, b1, (TA)xq.x, b3, (TA)xq.y);
   };
   fwd(S_E, 1, 0);
   fwd(S_N, 0, 1);

@@ -491,6 +491,103 @@ __global__ void k_q2_refine_cells(int N, const double* __restrict__ src, double*
   dst[(long long)j * 2 * N + i] = src[(long long)(j >> 1) * N + (i >> 1)];
 }
 
+// Block-Jacobi inverse of the Q2 operator: the 2x2 diagonal block of every
+// interior node summed over the cells that contain it (local dof pairs
+// (2n, 2n+1) of K_e), inverted; 3 planes (xx, xy, yy) of gq.plane, 0 on the
+// boundary.
+__global__ void k_q2_dinv(int N, Layout gq, long long cpl, const double* __restrict__ ke, double* __restrict__ dinv) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n1 = 2 * N + 1;
+  if (I >= n1 || J >= n1) return;
+  const long long nd = (long long)J * gq.ld + I;
+  double i00 = 0.0, i01 = 0.0, i11 = 0.0;
+  if (I >= 1 && J >= 1 && I <= n1 - 2 && J <= n1 - 2) {
+    int ci[2], ca[2], cj[2], cb[2], nx = 0, ny = 0;
+    if (I & 1) {
+      ci[nx] = I >> 1; ca[nx++] = 1;
+    } else {
+      if ((I >> 1) - 1 >= 0) { ci[nx] = (I >> 1) - 1; ca[nx++] = 2; }
+      if ((I >> 1) < N) { ci[nx] = I >> 1; ca[nx++] = 0; }
+    }
+    if (J & 1) {
+      cj[ny] = J >> 1; cb[ny++] = 1;
+    } else {
+      if ((J >> 1) - 1 >= 0) { cj[ny] = (J >> 1) - 1; cb[ny++] = 2; }
+      if ((J >> 1) < N) { cj[ny] = J >> 1; cb[ny++] = 0; }
+    }
+    double d00 = 0.0, d01 = 0.0, d11 = 0.0;
+    for (int u = 0; u < ny; ++u)
+      for (int t = 0; t < nx; ++t) {
+        const long long c = (long long)cj[u] * N + ci[t];
+        const int r = 2 * (3 * cb[u] + ca[t]);
+        d00 += ke[(long long)elem18(r, r) * cpl + c];
+        d01 += ke[(long long)elem18(r, r + 1) * cpl + c];
+        d11 += ke[(long long)elem18(r + 1, r + 1) * cpl + c];
+      }
+    const double det = d00 * d11 - d01 * d01;
+    i00 = d11 / det;
+    i01 = -d01 / det;
+    i11 = d00 / det;
+  }
+  dinv[nd] = i00;
+  dinv[gq.plane + nd] = i01;
+  dinv[2 * gq.plane + nd] = i11;
+}
+
+// One Chebyshev step on the Q2 operator (Saad, Alg. 12.1 on D^-1 A, step
+// coefficients coef[2 k], coef[2 k + 1] from launch_cheb_coefs):
+//   d <- c1 d + c2 D^-1 (b - Ax),  x <- x + d     (Ax = A x given).
+__global__ void k_q2_cheb_step(long long n, const double* __restrict__ dinv, long long pl,
+                               const double* __restrict__ coef, int k, const double2* __restrict__ b,
+                               const double2* __restrict__ Ax, double2* __restrict__ x, double2* __restrict__ d) {
+  const double c1 = coef[2 * k], c2 = coef[2 * k + 1];
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const double rx = b[t].x - Ax[t].x, ry = b[t].y - Ax[t].y;
+    const double i00 = dinv[t], i01 = dinv[pl + t], i11 = dinv[2 * pl + t];
+    double2 dd = d[t];
+    dd.x = c1 * dd.x + c2 * (i00 * rx + i01 * ry);
+    dd.y = c1 * dd.y + c2 * (i01 * rx + i11 * ry);
+    d[t] = dd;
+    double2 xx = x[t];
+    xx.x += dd.x;
+    xx.y += dd.y;
+    x[t] = xx;
+  }
+}
+
+// y <- D^-1 x (the power iteration for lambda_max(D^-1 A)).
+__global__ void k_q2_dinv_apply(long long n, const double* __restrict__ dinv, long long pl,
+                                const double2* __restrict__ x, double2* __restrict__ y) {
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (long long)gridDim.x * blockDim.x) {
+    const double i00 = dinv[t], i01 = dinv[pl + t], i11 = dinv[2 * pl + t];
+    const double2 v = x[t];
+    y[t] = make_double2(i00 * v.x + i01 * v.y, i01 * v.x + i11 * v.y);
+  }
+}
+
+// Dual state of the Q1 operator on the 2N grid from the Q2 one: Q1 cell (I, J)
+// is sub-cell (I & 1, J & 1) of Q2 cell (I/2, J/2), and its Gauss point
+// (qa, qb) lies nearest to the Q2 point (a + qa, b + qb) (Q1 points at cell
+// coordinates 0.106, 0.394, 0.606, 0.894; Q2 points at 0.113, 0.5, 0.887).
+__global__ void k_q2_pi_to_q1(int N, long long cpl, Layout g1, const double* __restrict__ pi2,
+                              double* __restrict__ pi1) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  if (I >= 2 * N || J >= 2 * N) return;
+  const long long c2 = (long long)(J >> 1) * N + (I >> 1);
+  const long long c1 = (long long)J * g1.ld + I;
+  const int a = I & 1, b = J & 1;
+#pragma unroll
+  for (int qb = 0; qb < 2; ++qb)
+#pragma unroll
+    for (int qa = 0; qa < 2; ++qa) {
+      const int q1 = 2 * qb + qa, q2 = 3 * (b + qb) + (a + qa);
+#pragma unroll
+      for (int k = 0; k < 3; ++k) pi1[(3 * q1 + k) * g1.plane + c1] = pi2[(3 * q2 + k) * cpl + c2];
+    }
+}
+
 // dual state, caller layout ((j N + i) 9 + q) 3 + c  <->  27 planes of cpl
 __global__ void k_q2_pi_layout(int N, long long cpl, const double* __restrict__ src, double* __restrict__ dst,
                                int to_planes) {
@@ -592,6 +689,27 @@ void launch_q2_apply(cudaStream_t s, const Q2Geom& q, const double* ke, const do
 void launch_q2_refine_cells(cudaStream_t s, int N, const double* src, double* dst) {
   note_launch();
   k_q2_refine_cells<<<q2_cell_grid(2 * N), kQBlk, 0, s>>>(N, src, dst);
+}
+inline unsigned q2_flat_blocks(long long n) {
+  const long long b = (n + 255) / 256;
+  return (unsigned)(b < 152 * 16 ? b : 152 * 16);
+}
+void launch_q2_dinv(cudaStream_t s, const Q2Geom& q, const double* ke, double* dinv) {
+  note_launch();
+  k_q2_dinv<<<q2_node_grid(2 * q.N + 1), kQBlk, 0, s>>>(q.N, q.gq, q.cpl, ke, dinv);
+}
+void launch_q2_cheb_step(cudaStream_t s, const Q2Geom& q, const double* dinv, const double* coef, int k,
+                         const double2* b, const double2* Ax, double2* x, double2* d) {
+  note_launch();
+  k_q2_cheb_step<<<q2_flat_blocks(q.gq.plane), 256, 0, s>>>(q.gq.plane, dinv, q.gq.plane, coef, k, b, Ax, x, d);
+}
+void launch_q2_dinv_apply(cudaStream_t s, const Q2Geom& q, const double* dinv, const double2* x, double2* y) {
+  note_launch();
+  k_q2_dinv_apply<<<q2_flat_blocks(q.gq.plane), 256, 0, s>>>(q.gq.plane, dinv, q.gq.plane, x, y);
+}
+void launch_q2_pi_to_q1(cudaStream_t s, const Q2Geom& q, const double* pi2, double* pi1) {
+  note_launch();
+  k_q2_pi_to_q1<<<q2_cell_grid(2 * q.N), kQBlk, 0, s>>>(q.N, q.cpl, q.gq, pi2, pi1);
 }
 void launch_q2_pi_layout(cudaStream_t s, const Q2Geom& q, const double* src, double* dst, bool to_planes) {
   note_launch();

@@ -97,6 +97,9 @@ struct svn_handle {
   // when set, the outer Krylov operator (the Q2 discretisation uses this
   // handle's V-cycle and FGMRES workspace around its own operator)
   std::function<void(const double2*, double2*)> outer;
+  // when set, the FGMRES preconditioner (the Q2 discretisation smooths on its
+  // own operator around this handle's V-cycle)
+  std::function<int(const double2*, double2*)> pre_op;
 
   // the V-cycle as a CUDA graph: input in lv[0].b, output in lv[0].x[1]
   cudaGraph_t vc_graph = nullptr;
@@ -493,7 +496,7 @@ void vcycle_record(svn_handle* h) {
 }
 
 // z = M^-1 r for level-0 FP64 vectors r, z (one V-cycle).
-int precondition(svn_handle* h, const double2* r, double2* z) {
+int precondition_mg(svn_handle* h, const double2* r, double2* z) {
   Level& l0 = h->lv[0];
   cudaStream_t s = h->stream;
   if (h->mixed)
@@ -542,6 +545,11 @@ int precondition(svn_handle* h, const double2* r, double2* z) {
     CK(cudaMemcpyAsync(z, l0.x[1], sizeof(double2) * l0.g.plane, cudaMemcpyDeviceToDevice, s));
   CKL();
   return SVN_OK;
+}
+
+int precondition(svn_handle* h, const double2* r, double2* z) {
+  if (h->pre_op) return h->pre_op(r, z);
+  return precondition_mg(h, r, z);
 }
 
 // y = K0 z (FP64 outer operator).
@@ -693,6 +701,8 @@ int check_params(svn_handle* h, const svn_params* p) {
   if (!(p->lmax_safety >= 1.0 && p->lmax_safety < 4.0)) return fail(h, SVN_ERR_ARG, "lmax_safety must be in [1, 4)");
   if (p->cheb_fuse < 0 || p->cheb_fuse > 5) return fail(h, SVN_ERR_ARG, "cheb_fuse must be in [0, 5]");
   if (p->wait_polls < 0) return fail(h, SVN_ERR_ARG, "wait_polls must be >= 0");
+  if (p->q2_smooth_degree < 0 || p->q2_smooth_degree > 16)
+    return fail(h, SVN_ERR_ARG, "q2_smooth_degree must be in [0, 16]");
   if (p->cheb_degree_coarse < 0 || p->cheb_degree_coarse > 16)
     return fail(h, SVN_ERR_ARG, "cheb_degree_coarse must be in [0, 16]");
   if (!(p->retry_alpha >= 0.0 && p->retry_alpha <= 1.0)) return fail(h, SVN_ERR_ARG, "retry_alpha must be in [0, 1]");
@@ -1107,10 +1117,12 @@ int step_impl(svn_handle* h, double dt, double tol, svn_stats* st) {
 // ---- Q2 velocity elements ----------------------------------------------------------
 // The Q2 step owns its cell and quadrature data and borrows a Q1 handle on the
 // 2N grid (the same (2N+1)^2 nodes): its FGMRES workspace, and its V-cycle of
-// the Q1 operator linearised at the same node velocities (with the Q1 points'
-// own pi = tau/Delta) as the preconditioner -- Q1 on the refined grid is
-// spectrally equivalent to Q2 on the coarse one, and FGMRES only needs an
-// approximate inverse.  The outer operator is the FP64 Q2 Jacobian.
+// the Q1 operator linearised at the same node velocities as the
+// preconditioner -- Q1 on the refined grid is spectrally equivalent to Q2 on
+// the coarse one, and FGMRES only needs an approximate inverse.  The Q1
+// operator takes the Q2 iterate's dual state at the nearest Q2 point (with its
+// own tau/Delta instead, FGMRES stalled at its iteration cap from 256^2 cells
+// on).  The outer operator is the FP64 Q2 Jacobian.
 }  // namespace
 
 struct svn_q2 {
@@ -1127,6 +1139,10 @@ struct svn_q2 {
   double *partial = nullptr, *scal = nullptr;
   bool have_forcing = false;
   double cur_dt = -1.0;
+  bool pre_pi_q2 = true;   // preconditioner linearised with the Q2 pi (else its own tau/Delta)
+  // Q2 smoother around the Q1 V-cycle (p-multigrid)
+  double *dinv2 = nullptr, *coef2 = nullptr, *lmax2 = nullptr;
+  double2 *px = nullptr, *pd = nullptr, *py = nullptr, *prc = nullptr, *pzc = nullptr;
 };
 
 namespace {
@@ -1186,6 +1202,14 @@ int q2_create_impl(svn_q2* Q, const svn_grid* g, const svn_params* p, void* stre
                                       (size_t)q2_energy_partials(Q->q) * (2 * MAX_ALPHA + 1), 4096});
   TRY(dalloc(h, &Q->partial, np));
   TRY(dalloc(h, &Q->scal, 64));
+  TRY(dalloc(h, &Q->dinv2, 3 * pl));
+  TRY(dalloc(h, &Q->coef2, 2 * 16 + 2));
+  TRY(dalloc(h, &Q->lmax2, 1));
+  TRY(dalloc(h, &Q->px, pl));
+  TRY(dalloc(h, &Q->pd, pl));
+  TRY(dalloc(h, &Q->py, pl));
+  TRY(dalloc(h, &Q->prc, pl));
+  TRY(dalloc(h, &Q->pzc, pl));
   return SVN_OK;
 }
 
@@ -1194,6 +1218,8 @@ void q2_destroy_impl(svn_q2* Q) {
   dfree(Q->h2); dfree(Q->A2); dfree(Q->P); dfree(Q->rhoH); dfree(Q->fq); dfree(Q->voq); dfree(Q->pi);
   dfree(Q->pi_scratch); dfree(Q->ke); dfree(Q->eb);
   dfree(Q->v); dfree(Q->dv); dfree(Q->vt); dfree(Q->R); dfree(Q->rhs); dfree(Q->partial); dfree(Q->scal);
+  dfree(Q->dinv2); dfree(Q->coef2); dfree(Q->lmax2);
+  dfree(Q->px); dfree(Q->pd); dfree(Q->py); dfree(Q->prc); dfree(Q->pzc);
   if (Q->pre) svn_destroy(Q->pre);
   Q->pre = nullptr;
 }
@@ -1252,11 +1278,70 @@ int q2_linearize(svn_q2* Q, const double2* v, const double* pi) {
     launch_q2_element_matrices(h->stream, Q->q, q2_phys(Q, Q->cur_dt), v, pi, Q->P, Q->rhoH, Q->voq, Q->ke);
   }
   CKL();
-  launch_pi_init(h->stream, h->g0, make_phys(h, h->g0, h->cur_dt), v, h->pi);
+  if (Q->pre_pi_q2)
+    launch_q2_pi_to_q1(h->stream, Q->q, pi, h->pi);   // the Q2 iterate's dual state
+  else
+    launch_pi_init(h->stream, h->g0, make_phys(h, h->g0, h->cur_dt), v, h->pi);
   CKL();
   TRY(linearize(h, v, h->pi));
   Q->pre->outer = [Q](const double2* x, double2* y) {
     launch_q2_apply(Q->pre->stream, Q->q, Q->ke, x, Q->eb, y);
+  };
+  const int deg = Q->prm.q2_smooth_degree;
+  if (deg <= 0) {
+    Q->pre->pre_op = nullptr;
+    return SVN_OK;
+  }
+  // Chebyshev-block-Jacobi smoothing on the Q2 operator: D^-1 from the element
+  // matrices, lambda_max(D^-1 A) by 10 power steps from the current residual
+  cudaStream_t s = h->stream;
+  const Layout& g = Q->q.gq;
+  launch_q2_dinv(s, Q->q, Q->ke, Q->dinv2);
+  CK(cudaMemcpyAsync(Q->px, Q->R, sizeof(double2) * g.plane, cudaMemcpyDeviceToDevice, s));
+  double nx = 0.0, ny = 0.0;
+  TRY(norm2(h, Q->px, &nx));
+  for (int k = 0; k < 10 && nx > 0.0; ++k) {
+    launch_scale_to(s, g, 1.0 / nx, Q->px, Q->px);
+    launch_q2_apply(s, Q->q, Q->ke, Q->px, Q->eb, Q->py);
+    launch_q2_dinv_apply(s, Q->q, Q->dinv2, Q->py, Q->px);
+    CKL();
+    TRY(norm2(h, Q->px, &ny));
+    nx = ny;
+  }
+  const double lmax = (nx > 0.0 && std::isfinite(nx) ? nx : 1.0) * Q->prm.lmax_safety;
+  double* hb = h->hostbuf;
+  hb[0] = lmax;
+  CK(cudaMemcpyAsync(Q->lmax2, hb, sizeof(double), cudaMemcpyHostToDevice, s));
+  launch_cheb_coefs<double>(s, Q->lmax2, Q->prm.cheb_lo, deg, Q->coef2);
+  CKL();
+  CK(cudaStreamSynchronize(s));   // hostbuf reuse
+  // M^-1 r: deg Chebyshev steps from 0, the Q1 V-cycle on the residual, deg steps again
+  Q->pre->pre_op = [Q, deg](const double2* r, double2* z) -> int {
+    svn_handle* hh = Q->pre;
+    svn_handle* h = hh;   // for the error macros
+    cudaStream_t st = hh->stream;
+    const Layout& gg = Q->q.gq;
+    const size_t bytes = sizeof(double2) * gg.plane;
+    CK(cudaMemsetAsync(Q->px, 0, bytes, st));
+    CK(cudaMemsetAsync(Q->pd, 0, bytes, st));
+    CK(cudaMemsetAsync(Q->py, 0, bytes, st));
+    for (int k = 0; k < deg; ++k) {
+      if (k > 0) launch_q2_apply(st, Q->q, Q->ke, Q->px, Q->eb, Q->py);
+      launch_q2_cheb_step(st, Q->q, Q->dinv2, Q->coef2, k, r, Q->py, Q->px, Q->pd);
+    }
+    launch_q2_apply(st, Q->q, Q->ke, Q->px, Q->eb, Q->py);
+    launch_axpby_to(st, gg, r, -1.0, Q->py, Q->prc);
+    CKL();
+    TRY(precondition_mg(hh, Q->prc, Q->pzc));
+    launch_axpy(st, gg, 1.0, Q->pzc, Q->px);
+    CK(cudaMemsetAsync(Q->pd, 0, bytes, st));
+    for (int k = 0; k < deg; ++k) {
+      launch_q2_apply(st, Q->q, Q->ke, Q->px, Q->eb, Q->py);
+      launch_q2_cheb_step(st, Q->q, Q->dinv2, Q->coef2, k, r, Q->py, Q->px, Q->pd);
+    }
+    CK(cudaMemcpyAsync(z, Q->px, bytes, cudaMemcpyDeviceToDevice, st));
+    CKL();
+    return SVN_OK;
   };
   return SVN_OK;
 }
@@ -1421,6 +1506,7 @@ int svn_default_params(svn_params* p) {
   p->mg_rebuild = 1;
   p->method = 0;
   p->retry_alpha = 1.0 / 64.0;
+  p->q2_smooth_degree = 2;
   return SVN_OK;
 }
 
