@@ -185,7 +185,7 @@ class ClockSampler:
 
 
 # Solver settings of the timed workload (chosen by the parameter sweeps).
-SETTINGS = dict(eisenstat_walker=1, krylov_rtol=1e-4, ew_eta_max=0.1, max_krylov=600, cheb_degree=6,
+SETTINGS = dict(eisenstat_walker=1, krylov_rtol=1e-3, ew_eta_max=0.03, max_krylov=600, cheb_degree=6,
                 cheb_lo=0.02, coarse_N=4, lmax_iters=15)
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2070 MHz
 # DRAM traffic (read + write) per node of the finest-level two-step FP32 sweep
@@ -571,10 +571,10 @@ def run_q2(args):
     p = W.make_problem_q2(N, seed=2)
     t = lambda a: torch.as_tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
     out = {}
-    for prec in ("mixed", "fp64"):
+    for prec in (("mixed",) if args.no_fp64 else ("mixed", "fp64")):
         s = Q2Solver(N, p.L, **dict(SETTINGS, precision=prec, restart=100, max_krylov=1000))
         s.set_forcing(t(p.h), t(p.A), t(p.wind), t(p.ocean), t(p.v_old))
-        for _ in range(max(1, args.warmup)):
+        for _ in range(args.warmup):
             s.step(p.dt, args.tol)
         torch.cuda.synchronize()
         times, st = [], None
@@ -594,7 +594,7 @@ def run_q2(args):
             "steps": args.steps, "warmup": args.warmup, "data": "synthetic",
             "config": {"workload": "svN implicit step on %dx%d Q2 cells (%d DOF, the nodes of the %dx%d Q1 "
                                    "workload), dt=1800 s, Delta_min=2e-9" % (N, N, dof, 2 * N, 2 * N)},
-            "mixed": out["mixed"], "fp64": out["fp64"]}
+            "mixed": out["mixed"], "fp64": out.get("fp64")}
 
 
 def run_learned_c4(args):

@@ -138,7 +138,7 @@ typedef struct svn_params {
                                each Krylov solve; the counter is device-wide) */
   int q2_smooth_degree;     /* Q2 elements only: Chebyshev-block-Jacobi steps on the Q2
                                operator before and after the Q1 V-cycle of the
-                               preconditioner (p-multigrid; default 2, 0: the Q1 V-cycle
+                               preconditioner (p-multigrid; default 3, 0: the Q1 V-cycle
                                alone) */
 } svn_params;
 

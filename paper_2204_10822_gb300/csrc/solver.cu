@@ -1506,7 +1506,7 @@ int svn_default_params(svn_params* p) {
   p->mg_rebuild = 1;
   p->method = 0;
   p->retry_alpha = 1.0 / 64.0;
-  p->q2_smooth_degree = 2;
+  p->q2_smooth_degree = 3;
   return SVN_OK;
 }
 

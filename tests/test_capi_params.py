@@ -30,7 +30,7 @@ def test_defaults_match_the_header():
     assert p.krylov_rtol == 1e-6 and p.restart == 30 and p.cheb_degree == 3 and p.coarse_N == 4
     assert p.precision == capi.SVN_FP64 and p.method == 0 and p.cheb_fuse == 1 and p.cheb_degree_coarse == 0
     assert p.lmax_iters == 15 and p.lmax_safety == 1.15 and p.use_graphs == 1 and p.vcycle_fp32 == 1
-    assert p.retry_alpha == 1.0 / 64.0 and p.wait_polls == 0 and p.q2_smooth_degree == 2
+    assert p.retry_alpha == 1.0 / 64.0 and p.wait_polls == 0 and p.q2_smooth_degree == 3
 
 
 def create(grid, params):
