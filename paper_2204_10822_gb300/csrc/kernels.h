@@ -82,6 +82,7 @@ void launch_q2_dinv(cudaStream_t s, const Q2Geom& q, const double* ke, double* d
 void launch_q2_cheb_step(cudaStream_t s, const Q2Geom& q, const double* dinv, const double* coef, int k,
                          const double2* b, const double2* Ax, double2* x, double2* d);
 void launch_q2_dinv_apply(cudaStream_t s, const Q2Geom& q, const double* dinv, const double2* x, double2* y);
+void launch_q2_checker(cudaStream_t s, const Q2Geom& q, double2* x);   // power-iteration start vector
 // pi of the Q1 operator on the 2N grid (12 planes of gq.plane) from the Q2 pi
 void launch_q2_pi_to_q1(cudaStream_t s, const Q2Geom& q, const double* pi2, double* pi1);
 

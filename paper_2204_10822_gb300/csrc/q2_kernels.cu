@@ -556,6 +556,18 @@ __global__ void k_q2_cheb_step(long long n, const double* __restrict__ dinv, lon
   }
 }
 
+// Start vector of the power iteration: a checkerboard in both components on
+// the interior nodes (all the high-frequency modes the smoother must damp).
+__global__ void k_q2_checker(int N, Layout gq, double2* __restrict__ x) {
+  const int I = blockIdx.x * blockDim.x + threadIdx.x;
+  const int J = blockIdx.y * blockDim.y + threadIdx.y;
+  const int n1 = 2 * N + 1;
+  if (I >= n1 || J >= n1) return;
+  const bool in = I >= 1 && J >= 1 && I <= n1 - 2 && J <= n1 - 2;
+  const double a = ((I + J) & 1) ? 1.0 : -1.0, b = (I & 1) ? 1.0 : -1.0;
+  x[(long long)J * gq.ld + I] = in ? make_double2(a, b) : make_double2(0.0, 0.0);
+}
+
 // y <- D^-1 x (the power iteration for lambda_max(D^-1 A)).
 __global__ void k_q2_dinv_apply(long long n, const double* __restrict__ dinv, long long pl,
                                 const double2* __restrict__ x, double2* __restrict__ y) {
@@ -702,6 +714,10 @@ void launch_q2_cheb_step(cudaStream_t s, const Q2Geom& q, const double* dinv, co
                          const double2* b, const double2* Ax, double2* x, double2* d) {
   note_launch();
   k_q2_cheb_step<<<q2_flat_blocks(q.gq.plane), 256, 0, s>>>(q.gq.plane, dinv, q.gq.plane, coef, k, b, Ax, x, d);
+}
+void launch_q2_checker(cudaStream_t s, const Q2Geom& q, double2* x) {
+  note_launch();
+  k_q2_checker<<<q2_node_grid(2 * q.N + 1), kQBlk, 0, s>>>(q.N, q.gq, x);
 }
 void launch_q2_dinv_apply(cudaStream_t s, const Q2Geom& q, const double* dinv, const double2* x, double2* y) {
   note_launch();

@@ -1293,14 +1293,16 @@ int q2_linearize(svn_q2* Q, const double2* v, const double* pi) {
     return SVN_OK;
   }
   // Chebyshev-block-Jacobi smoothing on the Q2 operator: D^-1 from the element
-  // matrices, lambda_max(D^-1 A) by 10 power steps from the current residual
+  // matrices, lambda_max(D^-1 A) by power steps from a checkerboard (a smooth
+  // start vector underestimates it, and Chebyshev then amplifies the top modes)
   cudaStream_t s = h->stream;
   const Layout& g = Q->q.gq;
   launch_q2_dinv(s, Q->q, Q->ke, Q->dinv2);
-  CK(cudaMemcpyAsync(Q->px, Q->R, sizeof(double2) * g.plane, cudaMemcpyDeviceToDevice, s));
+  launch_q2_checker(s, Q->q, Q->px);
+  CKL();
   double nx = 0.0, ny = 0.0;
   TRY(norm2(h, Q->px, &nx));
-  for (int k = 0; k < 10 && nx > 0.0; ++k) {
+  for (int k = 0; k < std::max(10, Q->prm.lmax_iters) && nx > 0.0; ++k) {
     launch_scale_to(s, g, 1.0 / nx, Q->px, Q->px);
     launch_q2_apply(s, Q->q, Q->ke, Q->px, Q->eb, Q->py);
     launch_q2_dinv_apply(s, Q->q, Q->dinv2, Q->py, Q->px);

@@ -2,13 +2,13 @@
 //
 // The same two Chebyshev steps as the other two-step kernels (Saad, Alg. 12.1
 // on D^-1 A: x1 = x0 + d1, x2 = x1 + d2 with d_{k+1} = c1 d_k + c2 D^-1 (b - A x_k)),
-// organised around the Tensor Memory Accelerator.  One CTA of 256 threads owns
-// a strip of 124 output columns and a chunk of rows; thread pair (2 t, 2 t + 1)
-// sits on column c0 - 2 + t and computes its x and y components.  Each row of the level's data -- the 19 stencil planes, the
+// organised around the Tensor Memory Accelerator.  One CTA of 128 threads owns
+// a strip of 124 output columns and a chunk of rows; thread t sits on column
+// c0 - 2 + t.  Each row of the level's data -- the 19 stencil planes, the
 // three block-Jacobi planes, b, d0 and x0 -- reaches shared memory as one
 // box of 132 columns per array (starting at c0 - 4, a 16-byte boundary), so a
 // row costs five cp.async.bulk.tensor instructions issued by one thread, and a
-// six-stage ring keeps rows q+2 and q+3 in flight while row q is computed.
+// six-stage ring keeps rows q+2 .. q+4 in flight while row q is computed.
 // Row q needs stencil rows q-1, q (own, E, N, NE, NW blocks and the
 // transposed blocks of its W, S, SW, SE neighbours) and x0 rows q-1 .. q+1
 // (step 1); step 2 runs one row behind on x1 rows q-2 .. q, which the CTA
@@ -33,8 +33,7 @@ namespace svn {
 
 namespace {
 
-constexpr int kTC = 128;        // columns per CTA
-constexpr int kTT = 2 * kTC;    // threads per CTA: one per column and velocity component
+constexpr int kTT = 128;        // threads per CTA, one column each
 constexpr int kTOut = 124;      // output columns per CTA
 constexpr int kTBox = 132;      // staged columns per row (from c0 - 4)
 constexpr int kTStages = 6;     // ring depth
@@ -48,8 +47,8 @@ constexpr int kOffB = align128(kOffInv + kBytesInv);
 constexpr int kOffD = align128(kOffB + kBytesV);
 constexpr int kOffX = align128(kOffD + kBytesV);
 constexpr int kStageBytes = align128(kOffX + kBytesV);
-constexpr int kOffRing = kTStages * kStageBytes;          // x1 ring, 3 rows x kTC float2
-constexpr int kOffBars = kOffRing + 3 * kTC * 8;
+constexpr int kOffRing = kTStages * kStageBytes;          // x1 ring, 3 rows x kTT float2
+constexpr int kOffBars = kOffRing + 3 * kTT * 8;
 constexpr int kSmemBytes = kOffBars + kTStages * 8;
 constexpr unsigned kDefaultPolls = 1u << 22;
 
@@ -150,29 +149,6 @@ __device__ __forceinline__ void row_apply(const float* __restrict__ Sq, const fl
   bwd(Sm, S_NW, c + 1, X(-1, 1));
 }
 
-// Component k (0: x, 1: y) of (A x) at one node of row q, staged column c (the
-// same couplings as row_apply; a thread pair computes the two components).
-template <typename XF>
-__device__ __forceinline__ float row_apply1(const float* __restrict__ Sq, const float* __restrict__ Sm, int c,
-                                            int k, XF X) {
-  auto at = [&](const float* S, int slot, int col) { return S[slot * kTBox + col]; };
-  const float2 xc = X(0, 0);
-  float y = at(Sq, S_D + k, c) * xc.x + at(Sq, S_D + 1 + k, c) * xc.y;
-  auto fwd = [&](int slot, float2 xq) { y += at(Sq, slot + 2 * k, c) * xq.x + at(Sq, slot + 2 * k + 1, c) * xq.y; };
-  auto bwd = [&](const float* S, int slot, int col, float2 xq) {
-    y += at(S, slot + k, col) * xq.x + at(S, slot + 2 + k, col) * xq.y;
-  };
-  fwd(S_E, X(0, 1));
-  fwd(S_N, X(1, 0));
-  fwd(S_NE, X(1, 1));
-  fwd(S_NW, X(1, -1));
-  bwd(Sq, S_E, c - 1, X(0, -1));
-  bwd(Sm, S_N, c, X(-1, 0));
-  bwd(Sm, S_NE, c - 1, X(-1, -1));
-  bwd(Sm, S_NW, c + 1, X(-1, 1));
-  return y;
-}
-
 // kPower: x1 = D^-1 A x0, x2 = D^-1 A x1 (power iteration, no b or d).
 // have_x0 == 0: start from x0 = d0 = 0 (the first pre-smoothing pass).
 template <bool kPower>
@@ -182,17 +158,16 @@ __global__ void __launch_bounds__(kTT) k_cheb_sweep2t(
     const __grid_constant__ CUtensorMap mX0, int have_x0, const float* __restrict__ coef, int step,
     float2* __restrict__ x2, float2* __restrict__ d2, int rows, int nstrips, unsigned polls) {
   extern __shared__ __align__(1024) unsigned char sm[];
-  float* ring = reinterpret_cast<float*>(sm + kOffRing);   // [3][kTC][2]
+  float2* ring = reinterpret_cast<float2*>(sm + kOffRing);
   uint64_t* bars = reinterpret_cast<uint64_t*>(sm + kOffBars);
   const int t = threadIdx.x;
-  const int tc = t >> 1, k = t & 1;   // column within the CTA, velocity component
   const int strip = blockIdx.x % nstrips, chunk = blockIdx.x / nstrips;
   const int j_lo = chunk * rows;
   if (j_lo > g.N) return;   // uniform over the CTA
   const int j_hi = min(j_lo + rows, g.N + 1);
   const int c0 = strip * kTOut;
-  const int i = c0 - 2 + tc;         // this thread's column
-  const int c = tc + 2;              // its staged column
+  const int i = c0 - 2 + t;          // this thread's column
+  const int c = t + 2;               // its staged column
   const int xbox = c0 - 4;           // multiple of 4: 16-byte aligned box start
   const int r0 = j_lo - 3, r_last = j_hi + 1;
   const bool load_d = !kPower && have_x0;
@@ -201,10 +176,9 @@ __global__ void __launch_bounds__(kTT) k_cheb_sweep2t(
   const float c1a = kPower ? 0.f : coef[2 * step], c2a = kPower ? 0.f : coef[2 * step + 1];
   const float c1b = kPower ? 0.f : coef[2 * step + 2], c2b = kPower ? 0.f : coef[2 * step + 3];
   const float2 zero = make_float2(0.f, 0.f);
-  auto comp = [&](float2 v) { return k ? v.y : v.x; };
 
   if (t == 0) {
-    for (int s2 = 0; s2 < kTStages; ++s2) mbar_init(saddr(&bars[s2]));
+    for (int s = 0; s < kTStages; ++s) mbar_init(saddr(&bars[s]));
     asm volatile("fence.mbarrier_init.release.cluster;\n fence.proxy.async.shared::cta;" ::: "memory");
   }
   __syncthreads();
@@ -227,14 +201,13 @@ __global__ void __launch_bounds__(kTT) k_cheb_sweep2t(
         if (load_x) tma_2d(saddr(st + kOffX), &mX0, xbox, r, bar);
       }
     } else {
-      uint4* p4 = reinterpret_cast<uint4*>(st);
-      for (int e = t; e < kStageBytes / 16; e += kTT) p4[e] = make_uint4(0u, 0u, 0u, 0u);
+      uint4* p = reinterpret_cast<uint4*>(st);
+      for (int k = t; k < kStageBytes / 16; k += kTT) p[k] = make_uint4(0u, 0u, 0u, 0u);
       __syncthreads();
       if (t == 0) mbar_arrive(bar);
     }
   };
   bool failed = false;
-  // the barrier of every wait also ends all reads of the previous iteration
   auto wait_row = [&](int r) {
     const bool ok = mbar_wait(saddr(&bars[slot_of(r)]), parity_of(r), polls);
     failed = __syncthreads_or(!ok) != 0;
@@ -247,80 +220,70 @@ __global__ void __launch_bounds__(kTT) k_cheb_sweep2t(
     waited = r;
   }
 
-  float d1p = 0.f;   // this thread's component of d1 at its node of the previous row
+  float2 d1p = zero;   // d1 at this thread's node of the previous row
   for (int q = j_lo - 1; q <= j_hi && !failed; ++q) {
     wait_row(q + 1);
     if (failed) break;
     waited = q + 1;
-    // row q - 3's slot was read for the last time in iteration q - 1 (its step 2)
-    if (q > j_lo - 1) prefetch(q + kTStages - 3);
-    // step 1 at row q: thread (tc, k) computes component k; the pair swaps residuals
+    // step 1 at row q
     const StageView Vq = stage_view(stage(q)), Vm = stage_view(stage(q - 1)), Vp = stage_view(stage(q + 1));
-    const bool act1 = tc >= 1 && tc <= kTC - 2 && i >= 1 && i <= g.N - 1 && q >= 1 && q <= g.N - 1;
-    float y = 0.f;
-    if (act1) {
+    float2 x1 = zero, d1 = zero;
+    if (t >= 1 && t <= kTT - 2 && i >= 1 && i <= g.N - 1 && q >= 1 && q <= g.N - 1) {
+      float yx, yy;
       auto X0 = [&](int dr, int dc) {
         if (!load_x) return zero;
         const float2* xr = dr < 0 ? Vm.x0 : dr > 0 ? Vp.x0 : Vq.x0;
         return xr[c + dc];
       };
-      y = row_apply1(Vq.S, Vm.S, c, k, X0);
-    }
-    float x1 = 0.f, d1 = 0.f;
-    {
-      const float i0 = Vq.inv[k * kTBox + c], i1 = Vq.inv[(k + 1) * kTBox + c];   // row k of D^-1
+      row_apply(Vq.S, Vm.S, c, X0, yx, yy);
+      const float i00 = Vq.inv[c], i01 = Vq.inv[kTBox + c], i11 = Vq.inv[2 * kTBox + c];
       if constexpr (kPower) {
-        const float yo = __shfl_xor_sync(0xffffffffu, y, 1);
-        x1 = k ? i0 * yo + i1 * y : i0 * y + i1 * yo;
+        x1 = make_float2(i00 * yx + i01 * yy, i01 * yx + i11 * yy);
       } else {
-        const float rme = comp(Vq.b[c]) - y;
-        const float ro = __shfl_xor_sync(0xffffffffu, rme, 1);
-        const float z = k ? i0 * ro + i1 * rme : i0 * rme + i1 * ro;
-        const float dd = load_d ? comp(Vq.d0[c]) : 0.f;
-        const float xx = load_x ? comp(Vq.x0[c]) : 0.f;
-        d1 = c1a * dd + c2a * z;
-        x1 = xx + d1;
+        const float2 bb = Vq.b[c];
+        const float rx = bb.x - yx, ry = bb.y - yy;
+        const float2 dd = load_d ? Vq.d0[c] : zero;
+        const float2 xx = load_x ? Vq.x0[c] : zero;
+        d1 = make_float2(c1a * dd.x + c2a * (i00 * rx + i01 * ry), c1a * dd.y + c2a * (i01 * rx + i11 * ry));
+        x1 = make_float2(xx.x + d1.x, xx.y + d1.y);
       }
-      if (!act1) x1 = d1 = 0.f;
     }
-    ring[((q + 3) % 3) * 2 * kTC + t] = x1;
+    ring[((q + 3) % 3) * kTT + t] = x1;
     __syncthreads();
     // step 2 at row p = q - 1
     const int p = q - 1;
-    const bool out2 = p >= j_lo && tc >= 2 && tc <= kTC - 3 && i <= g.N;
-    const bool act2 = out2 && i >= 1 && i <= g.N - 1 && p >= 1 && p <= g.N - 1;
-    float y2 = 0.f;
-    auto X1 = [&](int dr, int dc) {
-      const float* rr = ring + ((p + dr + 3) % 3) * 2 * kTC + 2 * (tc + dc);
-      return make_float2(rr[0], rr[1]);
-    };
-    if (act2) y2 = row_apply1(Vm.S, stage_view(stage(p - 1)).S, c, k, X1);
-    {
-      const float i0 = Vm.inv[k * kTBox + c], i1 = Vm.inv[(k + 1) * kTBox + c];
-      float out = 0.f, dd = 0.f;
-      if constexpr (kPower) {
-        const float yo = __shfl_xor_sync(0xffffffffu, y2, 1);
-        out = k ? i0 * yo + i1 * y2 : i0 * y2 + i1 * yo;
-      } else {
-        const float rme = comp(Vm.b[c]) - y2;
-        const float ro = __shfl_xor_sync(0xffffffffu, rme, 1);
-        const float z = k ? i0 * ro + i1 * rme : i0 * rme + i1 * ro;
-        dd = c1b * d1p + c2b * z;
-        out = ring[((p + 3) % 3) * 2 * kTC + t] + dd;
+    if (p >= j_lo && t >= 2 && t <= kTT - 3 && i <= g.N) {
+      float2 out = zero;
+      if (i >= 1 && i <= g.N - 1 && p >= 1 && p <= g.N - 1) {
+        float yx, yy;
+        auto X1 = [&](int dr, int dc) { return ring[((p + dr + 3) % 3) * kTT + t + dc]; };
+        row_apply(Vm.S, stage_view(stage(p - 1)).S, c, X1, yx, yy);
+        const float i00 = Vm.inv[c], i01 = Vm.inv[kTBox + c], i11 = Vm.inv[2 * kTBox + c];
+        const float2 x1o = X1(0, 0);
+        const long long np = (long long)p * g.ld + i;
+        if constexpr (kPower) {
+          out = make_float2(i00 * yx + i01 * yy, i01 * yx + i11 * yy);
+        } else {
+          const float2 bb = Vm.b[c];
+          const float rx = bb.x - yx, ry = bb.y - yy;
+          const float2 dd = make_float2(c1b * d1p.x + c2b * (i00 * rx + i01 * ry),
+                                        c1b * d1p.y + c2b * (i01 * rx + i11 * ry));
+          d2[np] = dd;
+          out = make_float2(x1o.x + dd.x, x1o.y + dd.y);
+        }
       }
-      const long long np = (long long)p * g.ld + i;
-      if (act2 && !kPower) reinterpret_cast<float*>(d2)[2 * np + k] = dd;
-      if (out2) reinterpret_cast<float*>(x2)[2 * np + k] = act2 ? out : 0.f;
+      x2[(long long)p * g.ld + i] = out;
     }
     d1p = d1;
+    __syncthreads();          // every read of row q - 2's slot is done
+    prefetch(q + kTStages - 2);
   }
   if (failed) {
     // count the timeout, then wait (bounded) for the copies still in flight
     if (t == 0) {
       atomicAdd(&g_tma_timeouts, 1u);
-      // rows issued: the first kTStages, then row q + 3 at the start of every iteration
-      // q > j_lo - 1 that passed its wait; the last of those is q = waited - 1
-      const int issued = min(r_last, max(r0 + kTStages - 1, waited + 2));
+      // rows issued so far: the first kTStages, then row q + 3 by every finished iteration q - 1
+      const int issued = min(r_last, max(r0 + kTStages - 1, waited + 3));
       for (int r = waited + 1; r <= issued; ++r) mbar_wait(saddr(&bars[slot_of(r)]), parity_of(r), kDefaultPolls);
     }
     __syncthreads();
