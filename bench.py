@@ -266,6 +266,11 @@ def fp64_comparison(args, p, dev_in, v_mixed, stats_mixed, steps):
     res = {"s_per_step": statistics.mean(times), "s_per_step_min": min(times), "s_per_step_max": max(times),
            "timed_steps": steps, "newton_iters": st64["newton_iters"], "krylov_iters": st64["krylov_iters_total"],
            "rel_l2_mixed_vs_fp64": rel_l2(v_mixed, out64)}
+    # the accuracy reference: fixed Krylov tolerance 1e-6 (no forcing schedule),
+    # as in the full-size certificate test
+    s64.close()
+    s64 = Solver(N, p.L, **dict(SETTINGS, precision="fp64", eisenstat_walker=0, krylov_rtol=1e-6, max_newton=60))
+    s64.set_forcing(*dev_in)
     tight = torch.zeros_like(v_mixed)
     _, stt = s64.step(p.dt, 1e-10, out=tight, raise_on_error=False)
     if stt["status"] == "SVN_OK":
@@ -277,10 +282,17 @@ def fp64_comparison(args, p, dev_in, v_mixed, stats_mixed, steps):
     return res
 
 
+# Solver settings of the smaller-Delta_min comparison steps: the forcing range
+# [1e-4, 0.1] (robust at Delta_min 1e-10 for both precisions; the timed
+# workload's tighter range made the FP64 path run into its caps there) and a
+# Newton cap that bounds the run.
+SWEEP_SETTINGS = dict(SETTINGS, krylov_rtol=1e-4, ew_eta_max=0.1, max_newton=150)
+
+
 def delta_min_sweep(args, p, dev_in):
     """Mixed vs plain FP64 at the smaller Delta_min of the 2048^2 workload's sweep:
     one timed step each (after one warm-up), iteration counts and the mixed
-    solution's relative L2 distance from the FP64 one."""
+    solution's relative L2 distance from the FP64 one (SWEEP_SETTINGS)."""
     import dataclasses
 
     import torch
@@ -288,10 +300,10 @@ def delta_min_sweep(args, p, dev_in):
 
     rows = []
     for dmin in args.sweep_delta_min:
-        row = {"delta_min": dmin}
+        row = {"delta_min": dmin, "settings": "Eisenstat-Walker in [1e-4, 0.1], max 150 Newton iterations"}
         outs = {}
         for prec in ("mixed", "fp64"):
-            s = Solver(p.N, p.L, **dict(SETTINGS, precision=prec, vcycle_fp32=1 if prec == "mixed" else 0,
+            s = Solver(p.N, p.L, **dict(SWEEP_SETTINGS, precision=prec, vcycle_fp32=1 if prec == "mixed" else 0,
                                         delta_min=dmin))
             s.set_forcing(*dev_in)
             o = torch.zeros((p.N + 1, p.N + 1, 2), dtype=torch.float64, device="cuda")
@@ -315,6 +327,14 @@ def delta_min_sweep(args, p, dev_in):
     return rows
 
 
+_T0 = time.perf_counter()
+
+
+def phase(name):
+    """One progress line on stderr (the JSON line alone goes to stdout)."""
+    print(f"[bench {time.perf_counter() - _T0:8.1f} s] {name}", file=sys.stderr, flush=True)
+
+
 def run_ours(args, rank, world):
     import numpy as np
     import torch
@@ -333,6 +353,7 @@ def run_ours(args, rank, world):
     net, learned_info = None, None
     if mixed and not args.no_learned and N % 256 == 0:
         from paper_2204_10822_gb300.learned import Net, generate_pairs, he_init, train
+        phase("learned start: generating training pairs at 256^2")
         tl = time.perf_counter()
         pairs, _ = generate_pairs(256, n_traj=args.learned_traj, steps=4, seed0=10000,
                                   **dict(SETTINGS, precision="mixed", vcycle_fp32=1))
@@ -355,8 +376,10 @@ def run_ours(args, rank, world):
         if world > 1:
             torch.distributed.barrier()
 
+    phase("warm-up steps")
     for _ in range(args.warmup):
         s.step(p.dt, args.tol, out=out)
+    phase("timed steps")
     clocks = ClockSampler(local)
     if not args.no_clocks:
         clocks.start()
@@ -384,6 +407,7 @@ def run_ours(args, rank, world):
     # end to end through the C ABI with host buffers (pinned), copies inside
     e2e = None
     if not args.no_e2e:
+        phase("end-to-end steps through host buffers")
         pin = lambda a: torch.as_tensor(np.ascontiguousarray(a)).pin_memory()
         host_in = [pin(x) for x in (p.h, p.A, p.wind, p.ocean, p.v_old)]
         host_out = torch.zeros((N + 1, N + 1, 2), dtype=torch.float64).pin_memory()
@@ -404,9 +428,11 @@ def run_ours(args, rank, world):
     # the mixed solution stays in `out`, the FP64 one goes to its own buffer
     fp64 = None
     if mixed and not args.no_fp64:
+        phase("plain FP64 path")
         fp64 = fp64_comparison(args, p, dev_in, out, stats, min(args.steps, 3))
     sweep = None
     if mixed and not args.no_fp64 and not args.no_sweep and rank == 0:
+        phase("smaller Delta_min steps")
         sweep = delta_min_sweep(args, p, dev_in)
 
     result = None
@@ -772,6 +798,7 @@ def main():
         torch.distributed.init_process_group("nccl")
     cb = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        phase("oracle on the host cores")
         cb = cpu_baseline_obj()
     res = run_ours(args, rank, world)
     if rank == 0:
