@@ -140,6 +140,14 @@ typedef struct svn_params {
                                operator before and after the Q1 V-cycle of the
                                preconditioner (p-multigrid; default 3, 0: the Q1 V-cycle
                                alone) */
+  double ew_tail;           /* eisenstat_walker only: the forcing term of a Newton step
+                               is raised to min(ew_eta_max, ew_tail * tol * ||R_0|| /
+                               ||R_k||), so that a step whose residual is already near
+                               the stopping threshold is not solved far past it
+                               (Kelley, Iterative Methods for Linear and Nonlinear
+                               Equations, 1995, Sect. 6.3; no counterpart in the paper,
+                               which solves each linearisation directly).  Default
+                               0.5; 0 disables it; must be in [0, 1] */
 } svn_params;
 
 typedef struct svn_stats {

@@ -36,7 +36,8 @@ class SvnParams(ctypes.Structure):
         ("fused_trial", c_int),
         ("vcycle_fp32", c_int),
         ("cheb_degree_coarse", c_int),
-        ("retry_alpha", c_double), ("wait_polls", c_int), ("q2_smooth_degree", c_int)]
+        ("retry_alpha", c_double), ("wait_polls", c_int), ("q2_smooth_degree", c_int),
+        ("ew_tail", c_double)]
 
 
 class SvnStats(ctypes.Structure):

@@ -573,6 +573,28 @@ int norm2(svn_handle* h, const double2* x, double* out) {
   return SVN_OK;
 }
 
+// Relative Krylov tolerance of Newton iteration `it` (residual norm r, previous
+// norm r_prev, stopping threshold r_stop = tol ||R_0||).  Without
+// eisenstat_walker: krylov_rtol.  With it: Eisenstat-Walker choice 2,
+// eta_k = 0.9 (r_k / r_{k-1})^2, kept >= 0.9 eta_{k-1}^2 when that is above 0.1,
+// clipped to [krylov_rtol, ew_eta_max]; then, with ew_tail > 0, raised to
+// min(ew_eta_max, ew_tail r_stop / r_k) (Kelley 1995, Sect. 6.3): a step whose
+// residual is already near the threshold is not solved far beyond it.
+double forcing_term(const svn_params& p, int it, double r, double r_prev, double r_stop, double& eta_prev) {
+  if (!p.eisenstat_walker) return p.krylov_rtol;
+  double eta = p.ew_eta_max;
+  if (it > 0) {
+    const double ratio = r / r_prev;
+    eta = 0.9 * ratio * ratio;
+    const double prev = 0.9 * eta_prev * eta_prev;
+    if (prev > 0.1) eta = std::max(eta, prev);
+    eta = std::min(p.ew_eta_max, std::max(p.krylov_rtol, eta));
+  }
+  if (p.ew_tail > 0.0 && r > 0.0) eta = std::max(eta, std::min(p.ew_eta_max, p.ew_tail * r_stop / r));
+  eta_prev = eta;
+  return eta;
+}
+
 // FGMRES (right preconditioned, CGS2 Arnoldi) for K x = b, x = 0 on entry.
 int fgmres(svn_handle* h, const double2* b, double2* x, double rtol, int maxit, int* iters) {
   cudaStream_t s = h->stream;
@@ -706,6 +728,7 @@ int check_params(svn_handle* h, const svn_params* p) {
   if (p->cheb_degree_coarse < 0 || p->cheb_degree_coarse > 16)
     return fail(h, SVN_ERR_ARG, "cheb_degree_coarse must be in [0, 16]");
   if (!(p->retry_alpha >= 0.0 && p->retry_alpha <= 1.0)) return fail(h, SVN_ERR_ARG, "retry_alpha must be in [0, 1]");
+  if (!(p->ew_tail >= 0.0 && p->ew_tail <= 1.0)) return fail(h, SVN_ERR_ARG, "ew_tail must be in [0, 1]");
   return SVN_OK;
 }
 
@@ -1010,21 +1033,7 @@ int step_impl(svn_handle* h, double dt, double tol, svn_stats* st) {
     launch_neg_copy(s, g, h->R, h->rhs);
     CKL();
     int kits = 0;
-    double eta = p.krylov_rtol;
-    if (p.eisenstat_walker) {
-      // Eisenstat-Walker choice 2: eta_k = 0.9 (r_k / r_{k-1})^2 with the
-      // safeguard eta_k >= 0.9 eta_{k-1}^2 when that is above 0.1, clipped
-      // to [krylov_rtol, ew_eta_max]
-      eta = p.ew_eta_max;
-      if (it > 0) {
-        const double ratio = r / st->res_hist[it - 1];
-        eta = 0.9 * ratio * ratio;
-        const double prev = 0.9 * eta_prev * eta_prev;
-        if (prev > 0.1) eta = std::max(eta, prev);
-        eta = std::min(p.ew_eta_max, std::max(p.krylov_rtol, eta));
-      }
-      eta_prev = eta;
-    }
+    double eta = forcing_term(p, it, r, it > 0 ? st->res_hist[it - 1] : 0.0, tol * st->res0, eta_prev);
     // Inexact Newton safeguard: a loose Krylov tolerance on this ill-conditioned
     // operator can give a direction along which Phi barely decreases; when the
     // line search fails or accepts a step shorter than retry_alpha, the
@@ -1390,18 +1399,7 @@ int q2_step_impl(svn_q2* Q, double dt, double tol, svn_stats* st) {
     TRY(q2_linearize(Q, Q->v, Q->pi));
     launch_neg_copy(s, g, Q->R, Q->rhs);
     CKL();
-    double eta = p.krylov_rtol;
-    if (p.eisenstat_walker) {
-      eta = p.ew_eta_max;
-      if (it > 0) {
-        const double ratio = r / st->res_hist[it - 1];
-        eta = 0.9 * ratio * ratio;
-        const double prev = 0.9 * eta_prev * eta_prev;
-        if (prev > 0.1) eta = std::max(eta, prev);
-        eta = std::min(p.ew_eta_max, std::max(p.krylov_rtol, eta));
-      }
-      eta_prev = eta;
-    }
+    double eta = forcing_term(p, it, r, it > 0 ? st->res_hist[it - 1] : 0.0, tol * st->res0, eta_prev);
     // FGMRES on the Q2 operator, backtracking on Phi in batches of eight step
     // lengths per energy pass, and the retry_alpha safeguard of step_impl
     double alpha = 1.0, phi1 = 0.0, scale1 = 0.0;
@@ -1508,6 +1506,7 @@ int svn_default_params(svn_params* p) {
   p->mg_rebuild = 1;
   p->method = 0;
   p->retry_alpha = 1.0 / 64.0;
+  p->ew_tail = 0.5;
   p->q2_smooth_degree = 3;
   return SVN_OK;
 }

@@ -31,6 +31,7 @@ def test_defaults_match_the_header():
     assert p.precision == capi.SVN_FP64 and p.method == 0 and p.cheb_fuse == 1 and p.cheb_degree_coarse == 0
     assert p.lmax_iters == 15 and p.lmax_safety == 1.15 and p.use_graphs == 1 and p.vcycle_fp32 == 1
     assert p.retry_alpha == 1.0 / 64.0 and p.wait_polls == 0 and p.q2_smooth_degree == 3
+    assert p.ew_tail == 0.5
 
 
 def create(grid, params):
@@ -52,7 +53,7 @@ def create(grid, params):
     ("max_halvings", -1, "max_halvings"), ("e", 0.0, "physical"), ("delta_min", 0.0, "physical"),
     ("retry_alpha", -0.5, "retry_alpha"), ("retry_alpha", 2.0, "retry_alpha"),
     ("learned_rule", 5, "learned_rule"), ("learned_rule", -1, "learned_rule"),
-    ("q2_smooth_degree", 17, "q2_smooth_degree")])
+    ("q2_smooth_degree", 17, "q2_smooth_degree"), ("ew_tail", -0.1, "ew_tail"), ("ew_tail", 1.5, "ew_tail")])
 def test_bad_parameter_is_rejected(field, value, needle):
     p = defaults()
     setattr(p, field, value)
