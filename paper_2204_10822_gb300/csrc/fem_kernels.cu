@@ -434,11 +434,14 @@ __global__ void __launch_bounds__(128) k_element_matrices(Layout g, Phys ph, con
     A3[q] = s2 * s2 * C22;
     const double wx = voq[(2 * q) * g.plane + cell] - p.vx;
     const double wy = voq[(2 * q + 1) * g.plane + cell] - p.vy;
-    const double nw = sqrt(wx * wx + wy * wy);
+    // |w| and od / |w| from one reciprocal square root (no sqrt and division)
+    const double w2 = wx * wx + wy * wy;
+    const double iw = w2 > 0.0 ? rsqrt(w2) : 0.0;
+    const double nw = w2 * iw;
     const double od = ph.dt * ph.cdrag;
     double mxx = rh + od * nw, myy = rh + od * nw, mxy = 0.0;
     if (nw >= 1e-14) {
-      const double r1 = od / nw;
+      const double r1 = od * iw;
       mxx += r1 * wx * wx;
       myy += r1 * wy * wy;
       mxy = r1 * wx * wy;

@@ -345,15 +345,20 @@ def test_minimum_grid_and_restarted_fgmres():
 
 
 def test_line_search_exhaustion_is_reported():
-    # with zero halvings allowed a rejected unit step must end the step with
-    # SVN_ERR_LINESEARCH and leave a finite iterate
-    p = W.config(2, N=64)
-    s = make_solver(p, max_halvings=0, precision="mixed")
+    # stdN on the 32^2 base workload: the oracle first rejects the unit step at
+    # Newton iteration 3 (it accepts alpha = 1/8 there), so with no halvings
+    # allowed the oracle and the GPU path must both stop at that iteration with
+    # a line-search failure (Section 5.1's backtracking, exhausted), after the
+    # same residual history, and leave a finite iterate
+    p = W.config(0, N=32)
+    ref = newton(p, tol=1e-10, method="stdn", max_newton=200, max_halvings=0)
+    assert ref.status == "linesearch" and ref.newton_iters == 3
+    s = make_solver(p, method=1, krylov_rtol=1e-11, max_krylov=2000, max_halvings=0)
     v, st = s.step(p.dt, 1e-10, raise_on_error=False)
-    assert st["status"] in ("SVN_ERR_LINESEARCH", "SVN_OK")
+    assert st["status"] == "SVN_ERR_LINESEARCH", st["status"]
+    assert st["newton_iters"] == ref.newton_iters
+    np.testing.assert_allclose(st["res_hist"], ref.res_hist, rtol=1e-6)
     assert np.isfinite(host(v)).all()
-    if st["status"] == "SVN_OK":
-        assert st["halvings_total"] == 0
 
 
 def test_standard_newton_matches_oracle_stdn():
