@@ -193,11 +193,11 @@ SETTINGS = dict(eisenstat_walker=1, krylov_rtol=1e-3, ew_eta_max=0.03, restart=1
                 cheb_lo=0.02, coarse_N=4, lmax_iters=15)
 FP64_PEAK_TFLOPS = 2 * 2 * 152 * 2.070e9 / 1e12   # 2 DFMA/clk/SM x 152 SMs x 2070 MHz
 # DRAM traffic (read + write) per node of the finest-level two-step FP32 sweep
-# (row-streaming kernel k_cheb_sweep2s), from the ncu capture at 1024^2 in
-# profiles/k_cheb_sweep2s_fp32_1024.md (140.88 MB read + 8.64 MB written over
-# 1,057,800 padded nodes); set to None whenever that kernel changes until it is
-# captured again.
-SWEEP_TRAFFIC_PER_NODE = (140.884992e6 + 8.641024e6) / 1_057_800
+# (row-streaming kernel k_cheb_sweep2s, Chebyshev mode), from the ncu capture
+# of the current kernel at 1024^2 in profiles/k_cheb_sweep2s_fp32_1024.md (mean
+# of three launches: 140.886 MB read + 6.360 MB written over 1,057,800 padded
+# nodes); set to None whenever that kernel changes until it is captured again.
+SWEEP_TRAFFIC_PER_NODE = (140.886187e6 + 6.360405e6) / 1_057_800
 SWEEP_TRAFFIC_SOURCE = "ncu capture at 1024^2 scaled by nodes (profiles/k_cheb_sweep2s_fp32_1024.md)"
 
 
