@@ -18,7 +18,13 @@ its plain form so the CUDA kernels can be compared against it:
   * V-cycle: pre-smooth, restrict the residual, recurse, prolong, post-smooth,
     dense Cholesky on the coarsest level;
   * FGMRES with right preconditioning (Saad, Alg. 9.6), modified Gram-Schmidt
-    and Givens rotations.
+    and Givens rotations;
+  * optionally, on the finest levels, the smoothed prolongator of smoothed
+    aggregation (Vanek, Mandel, Brezina, "Algebraic multigrid by smoothed
+    aggregation for second and fourth order elliptic problems", Computing 56,
+    1996): P_s = (I - omega D^-1 A) P with omega = 4 / (3 lambda_max(D^-1 A)),
+    here applied to the bilinear P; the Galerkin operator P_s^T A P_s then
+    couples each coarse node to its 5 x 5 block neighbourhood.
 """
 from __future__ import annotations
 
@@ -127,6 +133,18 @@ def chebyshev(A, Dinv, b, x, degree, lmax, lo=0.1):
     return x
 
 
+def sa_omega(lmax):
+    """Damping of the prolongator smoother: 4 / (3 lambda_max(D^-1 A)), the
+    choice of Vanek, Mandel and Brezina (1996)."""
+    return 4.0 / (3.0 * lmax)
+
+
+def smoothed_prolongation(A, Dinv, P, omega):
+    """P_s = (I - omega D^-1 A) P: one damped block-Jacobi step applied to every
+    column of P."""
+    return (P - omega * (Dinv @ (A @ P))).tocsr()
+
+
 @dataclasses.dataclass
 class Level:
     A: sp.csr_matrix
@@ -136,25 +154,32 @@ class Level:
     chol: object = None
 
 
-def build_hierarchy(A0, N, coarse_N=8, lo=0.1, power_iters=0, safety=1.15):
+def build_hierarchy(A0, N, coarse_N=8, lo=0.1, power_iters=0, safety=1.15, smooth_levels=0):
     """Galerkin hierarchy N, N/2, ... down to ``coarse_N`` cells.
 
     lambda_max(D^-1 A) per level: the Gershgorin bound (power_iters = 0) or
-    the power-method estimate ``power_lmax``."""
-    levels = [Level(A0.tocsr())]
-    n = N
-    while n > coarse_N and n % 2 == 0:
-        P = prolongation(n // 2)
-        levels[-1].P = P
-        levels.append(Level(galerkin(levels[-1].A, P)))
-        n //= 2
-    n = N
-    for lv in levels[:-1]:
+    the power-method estimate ``power_lmax``.  The prolongators into the
+    ``smooth_levels`` finest levels are the smoothed ones of
+    ``smoothed_prolongation`` (omega from ``sa_omega`` of that level's
+    lambda_max estimate); the coarse operators stay Galerkin, P^T A P."""
+
+    def estimate(lv, n):
         lv.Dinv = block_diag_inverse(lv.A)
         if power_iters > 0:
             lv.lmax = power_lmax(lv.A, lv.Dinv, n, power_iters, safety)
         else:
             lv.lmax = gershgorin_lmax(lv.A, lv.Dinv)
+
+    levels = [Level(A0.tocsr())]
+    n = N
+    while n > coarse_N and n % 2 == 0:
+        lv = levels[-1]
+        estimate(lv, n)
+        P = prolongation(n // 2)
+        if len(levels) <= smooth_levels:
+            P = smoothed_prolongation(lv.A, lv.Dinv, P, sa_omega(lv.lmax))
+        lv.P = P
+        levels.append(Level(galerkin(lv.A, P)))
         n //= 2
     levels[-1].chol = sla.cho_factor(levels[-1].A.toarray(), lower=True)
     return levels
