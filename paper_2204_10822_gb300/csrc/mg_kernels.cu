@@ -448,10 +448,6 @@ template <>
 __device__ __forceinline__ float2 shup<float2>(float2 v) { return make_float2(shup(v.x), shup(v.y)); }
 template <>
 __device__ __forceinline__ float2 shdn<float2>(float2 v) { return make_float2(shdn(v.x), shdn(v.y)); }
-template <>
-__device__ __forceinline__ double2 shup<double2>(double2 v) { return make_double2(shup(v.x), shup(v.y)); }
-template <>
-__device__ __forceinline__ double2 shdn<double2>(double2 v) { return make_double2(shdn(v.x), shdn(v.y)); }
 
 template <typename T, typename TV>
 struct StreamRow {
@@ -499,7 +495,7 @@ __global__ void __launch_bounds__(128) k_cheb_sweep2s(Layout g, const TS* __rest
   };
 
   // carried between rows
-  TV x1p = zero, d1p = zero, x1pW = zero, x1pE = zero, x0W, x0E;
+  TV x1p = zero, d1p = zero, x1pW = zero, x1pE = zero, x0W = zero, x0E = zero;
   T eWp[4] = {T(0), T(0), T(0), T(0)};
   T a1x = 0, a1y = 0;                          // row q: couplings to row q-1 (x0)
   T a2px = 0, a2py = 0, a2cx = 0, a2cy = 0;    // rows q-1, q: couplings to the row below (x1)

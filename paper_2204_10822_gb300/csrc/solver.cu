@@ -996,7 +996,7 @@ int step_impl(svn_handle* h, double dt, double tol, svn_stats* st) {
     CKL();
   }
   h->state_set = false;   // a later step restarts from its own v^n unless set_state is called again
-  double phi0, scale0;
+  double phi0 = 0.0, scale0 = 0.0;
   {
     const double a0 = 0.0;
     TRY(energy(h, h->v, h->v, &a0, 1, &phi0, &scale0));
@@ -1374,7 +1374,7 @@ int q2_step_impl(svn_q2* Q, double dt, double tol, svn_stats* st) {
   launch_q2_pi_init(s, Q->q, ph, Q->v, Q->pi);
   CKL();
   const svn_params& p = Q->prm;
-  double phi0, scale0;
+  double phi0 = 0.0, scale0 = 0.0;
   {
     const double a0 = 0.0;
     TRY(q2_energy(Q, Q->v, Q->v, &a0, 1, &phi0, &scale0));
