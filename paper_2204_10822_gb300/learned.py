@@ -52,7 +52,8 @@ class Net:
 
     def set_params(self, p):
         p = np.ascontiguousarray(p, dtype=np.float32)
-        assert p.size == self.nparam
+        if p.size != self.nparam:
+            raise ValueError("params: expected %d float32 values, got %d" % (self.nparam, p.size))
         self._check(self.lib.svn_net_set_params(self.h, p.ctypes.data, self.nparam))
 
     def get_params(self):
@@ -68,8 +69,11 @@ class Net:
     def set_sample(self, slot, N, h, A, wind, ocean, v_old, v_target=None):
         import torch
         torch.cuda.current_stream().synchronize()
-        self._check(self.lib.svn_net_set_sample(self.h, slot, N, _ptr(h), _ptr(A), _ptr(wind), _ptr(ocean),
-                                                _ptr(v_old), _ptr(v_target) if v_target is not None else None))
+        nc, nv = N * N, 2 * (N + 1) ** 2
+        self._check(self.lib.svn_net_set_sample(self.h, slot, N, _ptr(h, nc, "h"), _ptr(A, nc, "A"),
+                                                _ptr(wind, nv, "wind"), _ptr(ocean, nv, "ocean"),
+                                                _ptr(v_old, nv, "v_old"),
+                                                _ptr(v_target, nv, "v_target") if v_target is not None else None))
 
     def forward(self, nb):
         out = np.empty((nb, self.G, self.G, 16), dtype=np.float32)

@@ -21,7 +21,15 @@ class SvnError(RuntimeError):
         self.status = capi.STATUS.get(code, str(code))
 
 
+PARAM_NAMES = frozenset(name for name, _ in capi.SvnParams._fields_)
+
+
 def default_params(**overrides) -> capi.SvnParams:
+    """The library's defaults with `overrides` applied; an unknown name is an
+    error (a misspelt setting would otherwise be ignored)."""
+    unknown = sorted(set(overrides) - PARAM_NAMES)
+    if unknown:
+        raise TypeError("unknown svn_params field(s): %s" % ", ".join(unknown))
     p = capi.SvnParams()
     capi.lib().svn_default_params(ctypes.byref(p))
     for k, v in overrides.items():
@@ -31,16 +39,36 @@ def default_params(**overrides) -> capi.SvnParams:
     return p
 
 
-def _ptr(t) -> int:
+def _check_numel(t, numel, name):
+    """The C ABI reads and writes exactly `numel` float64 values through a bare
+    pointer: a buffer of another size is refused here, before any call."""
+    n = int(t.numel()) if hasattr(t, "numel") and callable(t.numel) else int(np.size(t))
+    if numel is not None and n != numel:
+        raise ValueError("%s: expected %d float64 values, got %d" % (name, numel, n))
+
+
+def _ptr(t, numel=None, name="array") -> int:
     import torch
     if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float64 or not t.is_contiguous():
-        raise TypeError("expected a contiguous CUDA float64 tensor")
+        raise TypeError("%s: expected a contiguous CUDA float64 tensor" % name)
+    _check_numel(t, numel, name)
     return t.data_ptr()
 
 
-def _hptr(a) -> int:
+def _hptr(a, numel=None, name="array"):
     a = np.ascontiguousarray(a, dtype=np.float64)
+    _check_numel(a, numel, name)
     return a.ctypes.data, a
+
+
+def _host_out(out, numel, name="out"):
+    """A caller-supplied host result buffer: written in place, so it must be a
+    C-contiguous, writable float64 array of exactly `numel` values."""
+    if not (isinstance(out, np.ndarray) and out.dtype == np.float64 and out.flags.c_contiguous
+            and out.flags.writeable):
+        raise TypeError("%s: expected a writable C-contiguous float64 NumPy array" % name)
+    _check_numel(out, numel, name)
+    return out.ctypes.data
 
 
 class Solver:
@@ -49,6 +77,7 @@ class Solver:
     def __init__(self, N: int, L: float = 512e3, stream=None, **params):
         import torch
         self.N, self.L = int(N), float(L)
+        self.nc, self.nv, self.npi = self.N * self.N, 2 * (self.N + 1) ** 2, 12 * self.N * self.N
         self.lib = capi.lib()
         self.params = default_params(**params)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -93,17 +122,21 @@ class Solver:
         return torch.zeros(self.node_shape, dtype=torch.float64, device="cuda")
 
     # -- step ----------------------------------------------------------------
+    def _forcing_sizes(self):
+        return ((self.nc, "h"), (self.nc, "A"), (self.nv, "wind"), (self.nv, "ocean"), (self.nv, "v_old"))
+
     def set_forcing(self, h, A, wind, ocean, v_old):
-        self._check(self.lib.svn_set_forcing(self.h, _ptr(h), _ptr(A), _ptr(wind), _ptr(ocean), _ptr(v_old)))
+        ptrs = [_ptr(x, n, nm) for x, (n, nm) in zip((h, A, wind, ocean, v_old), self._forcing_sizes())]
+        self._check(self.lib.svn_set_forcing(self.h, *ptrs))
 
     def set_forcing_host(self, h, A, wind, ocean, v_old):
-        keep = [_hptr(x) for x in (h, A, wind, ocean, v_old)]
+        keep = [_hptr(x, n, nm) for x, (n, nm) in zip((h, A, wind, ocean, v_old), self._forcing_sizes())]
         self._check(self.lib.svn_set_forcing_host(self.h, *[k[0] for k in keep]))
 
     def step(self, dt: float, tol: float, out=None, raise_on_error: bool = True):
         out = self._vec() if out is None else out
         st = capi.SvnStats()
-        rc = self.lib.svn_step(self.h, dt, tol, _ptr(out), ctypes.byref(st))
+        rc = self.lib.svn_step(self.h, dt, tol, _ptr(out, self.nv, "out"), ctypes.byref(st))
         if rc != 0 and raise_on_error:
             self._check(rc)
         return out, st.to_dict()
@@ -111,7 +144,7 @@ class Solver:
     def step_host(self, dt: float, tol: float, out: np.ndarray | None = None, raise_on_error: bool = True):
         out = np.zeros(self.node_shape) if out is None else out
         st = capi.SvnStats()
-        rc = self.lib.svn_step_host(self.h, dt, tol, out.ctypes.data, ctypes.byref(st))
+        rc = self.lib.svn_step_host(self.h, dt, tol, _host_out(out, self.nv), ctypes.byref(st))
         if rc != 0 and raise_on_error:
             self._check(rc)
         return out, st.to_dict()
@@ -129,7 +162,7 @@ class Solver:
         import torch
         hc = torch.zeros((self.N, self.N), dtype=torch.float64, device="cuda")
         A = torch.zeros_like(hc)
-        self._check(self.lib.svn_get_ice(self.h, _ptr(hc), _ptr(A)))
+        self._check(self.lib.svn_get_ice(self.h, _ptr(hc, self.nc, "h"), _ptr(A, self.nc, "A")))
         return hc, A
 
     def advance(self, dt: float, tol: float, wind=None, ocean=None, out=None, raise_on_error: bool = True):
@@ -139,9 +172,9 @@ class Solver:
         out = self._vec() if out is None else out
         st = capi.SvnStats()
         n = ctypes.c_int()
-        rc = self.lib.svn_advance(self.h, dt, tol, _ptr(wind) if wind is not None else None,
-                                  _ptr(ocean) if ocean is not None else None, _ptr(out), ctypes.byref(st),
-                                  ctypes.byref(n))
+        rc = self.lib.svn_advance(self.h, dt, tol, _ptr(wind, self.nv, "wind") if wind is not None else None,
+                                  _ptr(ocean, self.nv, "ocean") if ocean is not None else None,
+                                  _ptr(out, self.nv, "out"), ctypes.byref(st), ctypes.byref(n))
         if rc != 0 and raise_on_error:
             self._check(rc)
         d = st.to_dict()
@@ -152,17 +185,18 @@ class Solver:
         import torch
         v = self._vec()
         pi = torch.zeros(self.pi_shape, dtype=torch.float64, device="cuda")
-        self._check(self.lib.svn_get_state(self.h, _ptr(v), _ptr(pi)))
+        self._check(self.lib.svn_get_state(self.h, _ptr(v, self.nv, "v"), _ptr(pi, self.npi, "pi")))
         return v, pi
 
     def set_state(self, v, pi):
-        self._check(self.lib.svn_set_state(self.h, _ptr(v), _ptr(pi)))
+        self._check(self.lib.svn_set_state(self.h, _ptr(v, self.nv, "v"), _ptr(pi, self.npi, "pi")))
 
     # -- hot-path components ---------------------------------------------------
     def residual(self, dt: float, v):
         R = self._vec()
         nrm = ctypes.c_double()
-        self._check(self.lib.svn_residual(self.h, dt, _ptr(v), _ptr(R), ctypes.byref(nrm)))
+        self._check(self.lib.svn_residual(self.h, dt, _ptr(v, self.nv, "v"), _ptr(R, self.nv, "R"),
+                                          ctypes.byref(nrm)))
         return R, nrm.value
 
     def energy(self, dt: float, v, dv, alphas):
@@ -170,29 +204,32 @@ class Solver:
         al = (ctypes.c_double * k)(*alphas)
         phi = (ctypes.c_double * k)()
         scale = ctypes.c_double()
-        self._check(self.lib.svn_energy(self.h, dt, _ptr(v), _ptr(dv), al, k, phi, ctypes.byref(scale)))
+        self._check(self.lib.svn_energy(self.h, dt, _ptr(v, self.nv, "v"), _ptr(dv, self.nv, "dv"), al, k, phi,
+                                        ctypes.byref(scale)))
         return list(phi), scale.value
 
     def linearize(self, dt: float, v, pi):
-        self._check(self.lib.svn_linearize(self.h, dt, _ptr(v), _ptr(pi)))
+        self._check(self.lib.svn_linearize(self.h, dt, _ptr(v, self.nv, "v"), _ptr(pi, self.npi, "pi")))
 
     def apply(self, x, level: int = 0):
         import torch
+        n = 2 * ((self.N >> level) + 1) ** 2 if level >= 0 else None
         y = torch.zeros_like(x)
-        self._check(self.lib.svn_apply(self.h, level, _ptr(x), _ptr(y)))
+        self._check(self.lib.svn_apply(self.h, level, _ptr(x, n, "x"), _ptr(y, n, "y")))
         return y
 
     def precondition(self, r):
         import torch
         z = torch.zeros_like(r)
-        self._check(self.lib.svn_precondition(self.h, _ptr(r), _ptr(z)))
+        self._check(self.lib.svn_precondition(self.h, _ptr(r, self.nv, "r"), _ptr(z, self.nv, "z")))
         return z
 
     def krylov_solve(self, b, rtol: float):
         import torch
         x = torch.zeros_like(b)
         its = ctypes.c_int()
-        self._check(self.lib.svn_krylov_solve(self.h, _ptr(b), _ptr(x), rtol, ctypes.byref(its)))
+        self._check(self.lib.svn_krylov_solve(self.h, _ptr(b, self.nv, "b"), _ptr(x, self.nv, "x"), rtol,
+                                              ctypes.byref(its)))
         return x, its.value
 
     # -- autotuner ---------------------------------------------------------------
@@ -261,7 +298,8 @@ class Solver:
         return int(capi.lib().svn_kernel_launches())
 
     def dual_update(self, dt: float, v, dv, alpha: float, pi):
-        self._check(self.lib.svn_dual_update(self.h, dt, _ptr(v), _ptr(dv), alpha, _ptr(pi)))
+        self._check(self.lib.svn_dual_update(self.h, dt, _ptr(v, self.nv, "v"), _ptr(dv, self.nv, "dv"), alpha,
+                                             _ptr(pi, self.npi, "pi")))
         return pi
 
 
@@ -301,7 +339,10 @@ class Batch:
     def set_forcing(self, i, h, A, wind, ocean, v_old):
         import torch
         torch.cuda.current_stream().synchronize()      # inputs are read on the instance's own stream
-        rc = self.lib.svn_set_forcing(self.handles[i], _ptr(h), _ptr(A), _ptr(wind), _ptr(ocean), _ptr(v_old))
+        N = self.Ns[i]
+        nc, nv = N * N, 2 * (N + 1) ** 2
+        rc = self.lib.svn_set_forcing(self.handles[i], _ptr(h, nc, "h"), _ptr(A, nc, "A"), _ptr(wind, nv, "wind"),
+                                      _ptr(ocean, nv, "ocean"), _ptr(v_old, nv, "v_old"))
         if rc != 0:
             raise SvnError(rc, self.lib.svn_last_error(self.handles[i]).decode())
 
@@ -311,7 +352,10 @@ class Batch:
         if outs is None:
             outs = [torch.zeros((N + 1, N + 1, 2), dtype=torch.float64, device="cuda") for N in self.Ns]
         torch.cuda.current_stream().synchronize()
-        ptrs = (ctypes.c_void_p * n)(*[_ptr(o) for o in outs])
+        if len(outs) != n:
+            raise ValueError("outs: expected %d buffers, got %d" % (n, len(outs)))
+        ptrs = (ctypes.c_void_p * n)(*[_ptr(o, 2 * (N + 1) ** 2, "outs[%d]" % i)
+                                       for i, (o, N) in enumerate(zip(outs, self.Ns))])
         stats = (capi.SvnStats * n)()
         rc = self.lib.svn_batch_step(self.b, dt, tol, ptrs, stats)
         if rc != 0:
@@ -326,6 +370,7 @@ class Q2Solver:
     def __init__(self, N: int, L: float = 512e3, stream=None, **params):
         import torch
         self.N, self.L = int(N), float(L)
+        self.nc, self.nv, self.npi = self.N * self.N, 2 * (2 * self.N + 1) ** 2, 27 * self.N * self.N
         self.lib = capi.lib()
         self.params = default_params(**params)
         self.stream = stream if stream is not None else torch.cuda.current_stream()
@@ -369,12 +414,14 @@ class Q2Solver:
         return torch.zeros(self.node_shape, dtype=torch.float64, device="cuda")
 
     def set_forcing(self, h, A, wind, ocean, v_old):
-        self._check(self.lib.svn_q2_set_forcing(self.h, _ptr(h), _ptr(A), _ptr(wind), _ptr(ocean), _ptr(v_old)))
+        self._check(self.lib.svn_q2_set_forcing(self.h, _ptr(h, self.nc, "h"), _ptr(A, self.nc, "A"),
+                                                _ptr(wind, self.nv, "wind"), _ptr(ocean, self.nv, "ocean"),
+                                                _ptr(v_old, self.nv, "v_old")))
 
     def step(self, dt: float, tol: float, out=None, raise_on_error: bool = True):
         out = self._vec() if out is None else out
         st = capi.SvnStats()
-        rc = self.lib.svn_q2_step(self.h, dt, tol, _ptr(out), ctypes.byref(st))
+        rc = self.lib.svn_q2_step(self.h, dt, tol, _ptr(out, self.nv, "out"), ctypes.byref(st))
         if rc != 0 and raise_on_error:
             self._check(rc)
         return out, st.to_dict()
@@ -382,7 +429,8 @@ class Q2Solver:
     def residual(self, dt: float, v):
         R = self._vec()
         nrm = ctypes.c_double()
-        self._check(self.lib.svn_q2_residual(self.h, dt, _ptr(v), _ptr(R), ctypes.byref(nrm)))
+        self._check(self.lib.svn_q2_residual(self.h, dt, _ptr(v, self.nv, "v"), _ptr(R, self.nv, "R"),
+                                             ctypes.byref(nrm)))
         return R, nrm.value
 
     def energy(self, dt: float, v, dv, alphas):
@@ -390,25 +438,27 @@ class Q2Solver:
         al = (ctypes.c_double * k)(*alphas)
         phi = (ctypes.c_double * k)()
         scale = ctypes.c_double()
-        self._check(self.lib.svn_q2_energy(self.h, dt, _ptr(v), _ptr(dv), al, k, phi, ctypes.byref(scale)))
+        self._check(self.lib.svn_q2_energy(self.h, dt, _ptr(v, self.nv, "v"), _ptr(dv, self.nv, "dv"), al, k, phi,
+                                           ctypes.byref(scale)))
         return list(phi), scale.value
 
     def linearize(self, dt: float, v, pi):
-        self._check(self.lib.svn_q2_linearize(self.h, dt, _ptr(v), _ptr(pi)))
+        self._check(self.lib.svn_q2_linearize(self.h, dt, _ptr(v, self.nv, "v"), _ptr(pi, self.npi, "pi")))
 
     def apply(self, x):
         import torch
         y = torch.zeros_like(x)
-        self._check(self.lib.svn_q2_apply(self.h, _ptr(x), _ptr(y)))
+        self._check(self.lib.svn_q2_apply(self.h, _ptr(x, self.nv, "x"), _ptr(y, self.nv, "y")))
         return y
 
     def dual_update(self, dt: float, v, dv, alpha: float, pi):
-        self._check(self.lib.svn_q2_dual_update(self.h, dt, _ptr(v), _ptr(dv), alpha, _ptr(pi)))
+        self._check(self.lib.svn_q2_dual_update(self.h, dt, _ptr(v, self.nv, "v"), _ptr(dv, self.nv, "dv"), alpha,
+                                                _ptr(pi, self.npi, "pi")))
         return pi
 
     def get_state(self):
         import torch
         v = self._vec()
         pi = torch.zeros(self.pi_shape, dtype=torch.float64, device="cuda")
-        self._check(self.lib.svn_q2_get_state(self.h, _ptr(v), _ptr(pi)))
+        self._check(self.lib.svn_q2_get_state(self.h, _ptr(v, self.nv, "v"), _ptr(pi, self.npi, "pi")))
         return v, pi
